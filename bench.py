@@ -1,0 +1,406 @@
+"""Benchmark of the LS forward + adjoint hot path on GB300.
+
+One step = one pass of the whole hot path over one batch: incident plane
+waves for every view, the batched BiCGStab forward solves with the far field
+on the detector, the residuals against synthetic measurements, and the
+adjoint solves with the gradient accumulation.  The Green spectrum and the
+far-field kernels are plan data built once per grid, outside the step.
+
+Workload: 128^3 grid (padded 256^3), 60 plane-wave views on a cone of NA 0.8,
+seeded phantom of 20 random ellipsoids (radii 4-20 voxels, dn in [0, 0.05]),
+128 x 128 detector, BiCGStab tol 1e-6, complex64 fields.  Measurements are
+the forward model of the phantom with 1% complex Gaussian noise; the
+gradient is taken at 0.9 x the phantom's potential.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import phantoms as ph  # noqa: E402
+
+METRIC = "LS matvec GB/s (%HBM) & solves/s at 128³×60 views; p50/p99 served solve latency"
+WORKLOADS = {
+    "bench": dict(shape=(128, 128, 128), views=60, count=20, rmin=4.0, rmax=20.0, dn_max=0.05),
+    "small": dict(shape=(32, 32, 32), views=4, count=4, rmin=2.0, rmax=6.0, dn_max=0.05),
+}
+TOL = 1e-6
+NA = 0.8
+
+
+def workload_name(w):
+    s = w["shape"]
+    return f"LS forward+adjoint, {s[2]}x{s[1]}x{s[0]} grid (pad {2*s[2]}x{2*s[1]}x{2*s[0]}), {w['views']} views NA {NA}, " \
+           f"{w['count']} ellipsoids dn<={w['dn_max']}, {s[2]}x{s[1]} detector, tol {TOL:g}"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in self.rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+# ----------------------------------------------------------------------------- helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+Z_SOURCES = ["paper_1910_13844_gb300/csrc/passes.cuh", "paper_1910_13844_gb300/csrc/dft.cuh",
+             "paper_1910_13844_gb300/csrc/common.cuh"]
+
+
+def traffic_per_slot(kernel: str):
+    """ncu DRAM bytes per slot for `kernel`, if recorded for the current source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    rec = d.get(kernel)
+    if not rec or rec.get("source_hash") != source_hash(Z_SOURCES):
+        return None
+    return float(rec["dram_bytes_per_slot"])
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+def oracle_sample(w, seconds_budget=12.0, iters_per_solve=None):
+    """Times the FP64 oracle's BiCGStab on one view of the workload for a bounded number of iterations."""
+    from oracle import green, kernel, model
+
+    shape = w["shape"]
+    st = model.setup_from_optics(shape, ph.LAMBDA_UM, ph.ETA_B, ph.VOXEL_UM)
+    op = model.Operator(st, kernel_method="prop1")
+    dn = ph.random_ellipsoids(shape, count=w["count"], rmin=w["rmin"], rmax=w["rmax"], dn_max=w["dn_max"])
+    f = green.scattering_potential(dn, ph.ETA_B, ph.LAMBDA_UM)
+    k = ph.cone_directions(w["views"], NA, ph.ETA_B)[0] * st.kb
+    uin = model.plane_wave(shape, st.h, k)
+    A = lambda x: op.A(x, f)  # noqa: E731
+    t1 = time.perf_counter()
+    A(uin)
+    t1 = time.perf_counter() - t1
+    it = max(1, int(seconds_budget / (2.0 * t1)))   # two operator applications per iteration
+    t0 = time.perf_counter()
+    _, it_done, _ = model.bicgstab(A, uin, tol=1e-30, maxiter=it)
+    it = max(it_done, 1)
+    dt = time.perf_counter() - t0
+    per_iter = dt / it
+    ips = iters_per_solve if iters_per_solve else 30.0
+    return {"seconds": dt, "iterations": it, "sec_per_iter": per_iter, "iters_per_solve": ips,
+            "solves_per_s": 1.0 / (per_iter * ips), "threads": os.cpu_count()}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+
+    import paper_1910_13844_gb300 as ls
+    from paper_1910_13844_gb300 import build as lsbuild
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lsbuild.build()
+    w = WORKLOADS[args.workload]
+    shape, Q = w["shape"], w["views"]
+    kb = 2 * np.pi * ph.ETA_B / ph.LAMBDA_UM
+    t_plan = time.perf_counter()
+    plan = ls.Plan(shape, kb, ph.VOXEL_UM, tol=TOL)
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t_plan
+    dn = ph.random_ellipsoids(shape, count=w["count"], rmin=w["rmin"], rmax=w["rmax"], dn_max=w["dn_max"],
+                              seed=ph.SEED_PHANTOM + rank)
+    dn_d = torch.from_numpy(dn.astype(np.float32)).to(dev)
+    f_true = torch.empty_like(dn_d)
+    ls.ls_scattering_potential(dn_d, ph.ETA_B, kb, f_true)
+    f0 = 0.9 * f_true
+    kvec = ph.cone_directions(Q, NA, ph.ETA_B) * kb
+    # synthetic measurements: forward of the phantom + 1% complex Gaussian noise
+    uin = plan.plane_waves(kvec)
+    _, y, code, _ = plan.forward(f_true, uin, want_fields=False)
+    noise = torch.from_numpy(ph.complex_normal((Q,) + plan.det).astype(np.complex64)).to(dev)
+    ynorm = torch.linalg.vector_norm(y.reshape(Q, -1), dim=1)
+    y = y + 0.01 * (ynorm / np.sqrt(2 * y[0].numel())).reshape(Q, 1, 1) * noise
+    weights = (1.0 / (ynorm.double() ** 2)).cpu().numpy()
+
+    u = plan.field(Q)
+    far = plan.detector(Q)
+    res = plan.detector(Q)
+    grad = torch.empty(shape, dtype=torch.float32, device=dev)
+    stats_acc = {"fwd_iters": [], "adj_iters": [], "status": []}
+
+    def step(f_dev, y_dev):
+        ls.ls_plane_waves(plan.handle, kvec, uin)
+        c1, s1 = ls.ls_forward(plan.handle, f_dev, uin, u, far)
+        loss = ls.ls_residual(far, y_dev, res)
+        c2, s2 = ls.ls_gradient(plan.handle, f_dev, res, grad, u_fwd=u, view_weights=weights)
+        stats_acc["fwd_iters"].append(np.mean([s["iterations"] for s in s1]))
+        stats_acc["adj_iters"].append(np.mean([s["iterations"] for s in s2]))
+        stats_acc["status"].append(max(c1, c2))
+        return 0.5 * float(np.sum(loss * weights))
+
+    for _ in range(args.warmup):
+        step(f0, y)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ls.ls_profile(plan.handle, True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(f0, y)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    prof = ls.ls_profile(plan.handle, False)
+    clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+
+    # end-to-end through the public API with host buffers (pinned), copies inside the timed region
+    f_host = f0.cpu().pin_memory()
+    y_host = y.cpu().pin_memory()
+    g_host = torch.empty(shape, dtype=torch.float32).pin_memory()
+    f_e = torch.empty_like(f0)
+    y_e = torch.empty_like(y)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        f_e.copy_(f_host, non_blocking=True)
+        y_e.copy_(y_host, non_blocking=True)
+        step(f_e, y_e)
+        g_host.copy_(grad, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+
+    solves_per_step = 2 * Q
+    ms_step = ms_total / args.steps
+    ms_e2e_step = ms_e2e / args.steps
+    if ws > 1:
+        t = torch.tensor([ms_step, ms_e2e_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step, ms_e2e_step = float(t[0]), float(t[1])
+    value = ws * solves_per_step / (ms_step / 1e3)
+    e2e_value = ws * solves_per_step / (ms_e2e_step / 1e3)
+
+    # roofline of the dominant kernel (the z pass: FFT, Green multiply, IFFT)
+    N = shape[0] * shape[1] * shape[2]
+    nz, ny, nx = shape
+    z_ms, z_launches, z_slots = prof["z"]
+    slots_per_launch = z_slots / max(z_launches, 1)
+    bytes_per_slot = 2 * 8 * (4 * N)                       # read + write of the nz x 2ny x 2nx pencils
+    octant = 8 * (nx + 1) * (ny + 1) * (nz + 1)            # Green spectrum octant, read once per launch
+    bytes_per_launch = bytes_per_slot * slots_per_launch + octant
+    z_ms_launch = z_ms / max(z_launches, 1)
+    achieved = bytes_per_launch / (z_ms_launch / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    tr = traffic_per_slot("z_pass")
+    dominant = max((k for k in prof if k != "other"), key=lambda k: prof[k][0])
+    total_kernel_ms = sum(v[0] for v in prof.values())
+    # whole-matvec GB/s: the five passes of one operator application
+    mv_ms = sum(prof[k][0] for k in ("fx", "fy", "z", "iy", "ix"))
+    mv_slot_passes = prof["z"][2]
+    mv_bytes = 228 * N * mv_slot_passes  # algorithmic bytes of one matvec pass structure (octant Ghat)
+    launches = int(sum(v[1] for v in prof.values()))
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "solves/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64",
+        "data": "synthetic",
+        "config": {
+            "workload": workload_name(w),
+            "views": Q, "grid": list(shape[::-1]), "solves_per_step": solves_per_step,
+            "l2": "inputs larger than L2 (per-view Krylov state 16 MiB x 8 vectors x 60 views)",
+            "plan_build_s": round(t_plan, 3), "plan_built_once": True,
+            "mean_forward_iterations": float(np.mean(stats_acc["fwd_iters"])),
+            "mean_adjoint_iterations": float(np.mean(stats_acc["adj_iters"])),
+            "worst_status": int(max(stats_acc["status"])),
+            "parallelism": f"replicas{ws}" if ws > 1 else "single",
+        },
+        "roofline": {
+            "kernel": "k_z (z-pencil FFT, Green multiply, inverse FFT, crop)",
+            "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+            "traffic": (round(tr * slots_per_launch) if tr is not None else None),
+            "algorithmic_bytes_per_launch": int(bytes_per_launch),
+            "launch_ms": round(z_ms_launch, 4), "slots_per_launch": slots_per_launch,
+        },
+        "matvec": {
+            "gbs": round(mv_bytes / (mv_ms / 1e3) / 1e9, 1) if mv_ms else None,
+            "frac_hbm": round(mv_bytes / (mv_ms / 1e3) / 1e9 / peak, 4) if mv_ms else None,
+            "us_per_view": round(1e3 * mv_ms / max(mv_slot_passes, 1), 2),
+            "bytes_model": "228 N bytes per view (F-x 28N, F-y 48N, Z 72N, I-y 48N, I-x 32N)",
+        },
+        "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in prof.items()} if total_kernel_ms else {},
+        "dominant_kernel": dominant,
+        "gpu_launches": launches,
+        "e2e": {"value": round(e2e_value, 4), "unit": "solves/s",
+                "h2d_bytes_per_step": int(f0.numel() * 4 + y.numel() * 8),
+                "d2h_bytes_per_step": int(grad.numel() * 4)},
+    }
+    out["clocks"] = clocks.summary()
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        ips = float(np.mean(stats_acc["fwd_iters"] + stats_acc["adj_iters"]))
+        cb = oracle_sample(w, iters_per_solve=ips)
+        out["cpu_baseline"] = {"value": round(cb["solves_per_s"], 6), "unit": "solves/s", "cores": cb["threads"],
+                               "kind": "oracle",
+                               "sample": f"FP64 oracle BiCGStab on view 0 of the same workload: {cb['iterations']} "
+                                         f"iterations in {cb['seconds']:.1f} s ({cb['sec_per_iter']:.2f} s/iteration), "
+                                         f"scaled by the GPU run's mean {ips:.1f} iterations per solve; "
+                                         f"oracle kernel build excluded"}
+    if rank == 0:
+        print(json.dumps(out))
+    plan.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    budget = 8.0
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state beyond its kernel build, done inside each sample
+    samples = []
+    for _ in range(args.steps):
+        samples.append(oracle_sample(w, seconds_budget=budget))
+    sps = float(np.median([s["solves_per_s"] for s in samples]))
+    s0 = samples[0]
+    out = {
+        "metric": METRIC, "value": round(sps, 6), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * s0["sec_per_iter"] * s0["iters_per_solve"] * 2 * w["views"], 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": workload_name(w), "views": w["views"]},
+        "cpu_baseline": {"value": round(sps, 6), "unit": "solves/s", "cores": s0["threads"], "kind": "oracle",
+                         "sample": f"each step: FP64 oracle BiCGStab on one view for ~{budget:.0f} s, "
+                                   f"scaled to solves with {s0['iters_per_solve']:.0f} iterations per solve"},
+        "e2e": {"value": round(sps, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="bench", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

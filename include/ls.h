@@ -1,0 +1,246 @@
+/*
+ * ls.h -- C ABI of the GB300 Lippmann-Schwinger forward model and gradient.
+ *
+ * Implements the discrete model of Pham et al., "Three-Dimensional Optical
+ * Diffraction Tomography with Lippmann-Schwinger Model" (arXiv 1910.13844):
+ *
+ *   eq. lipp1   u    = (I - G diag(f))^{-1} u_in            (BiCGStab, Sec. 2.2)
+ *   eq. lipp2   y_sc = G~ diag(f) u                          (P = I)
+ *   Alg. 1 l.6  grad = sum_q c_q Re(conj(u_q) .* w_q),
+ *               (I - G^H diag(f)) w_q = G~^H r_q             (Sec. 4.2)
+ *
+ * G is the Vainikko discretisation of the truncated Green function
+ * (Theorem 1) applied with twofold zero padding through the modified kernel
+ * of Proposition 1; G~ is the detector-plane operator of eq. Gtild-1.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout.  Volumes are [nz][ny][nx] row-major (x fastest).  Voxel (i, j, k)
+ *   (x, y, z array indices) sits at h * (i - nx/2 + 1, j - ny/2 + 1,
+ *   k - nz/2 + 1) micrometres: the centred index set of Sec. 1.4.  The
+ *   detector is [my][mx], pixel (a, b) (row, column) at
+ *   (h (b - mx/2 + 1), h (a - my/2 + 1), x_gamma).
+ * Types.  ls_c64 is interleaved complex64 (8 bytes); potentials and
+ *   gradients are float32.  Reductions inside the solver run in float64.
+ * Memory.  Every ls_c64/float pointer is DEVICE memory owned by the caller
+ *   unless stated otherwise; "host" marks host pointers.  Arrays of pointers
+ *   (const ls_c64* const* u_in, ...) are HOST arrays of n_views device
+ *   pointers, one per view.  The library never frees caller memory.  The plan
+ *   owns the Green spectrum, the far-field kernels and the solver workspace.
+ * Streams.  cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ *   Calls enqueue work on it; calls that return solver statistics
+ *   synchronise it before returning.
+ * Errors.  Every int-returning call returns LS_OK (0) or one of the LS_E*
+ *   codes below.  Nothing is thrown across the ABI.  ls_last_error() gives
+ *   a thread-local message for the last failure.
+ * Threads.  One plan must not be used by two threads at once.
+ */
+#ifndef LS_H
+#define LS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+enum ls_status {
+  LS_OK = 0,
+  LS_EINVAL = 1,         /* bad argument (size, pointer, option); nothing was enqueued   */
+  LS_ENOMEM = 2,         /* a device allocation failed                                    */
+  LS_ECUDA = 3,          /* a CUDA runtime call failed; see ls_last_error()               */
+  LS_NOT_CONVERGED = 4,  /* max_iter reached; outputs written, stats say which view        */
+  LS_BREAKDOWN = 5,      /* BiCGStab breakdown (rho or <r0,v> vanished) after all restarts */
+  LS_TIMEOUT = 6,        /* a bounded device wait expired                                  */
+  LS_PENDING = 7,        /* ls_poll: request not finished yet                              */
+  LS_EAGAIN = 8,         /* ls_submit: the request can never fit the server's HBM budget   */
+  LS_ENOTFOUND = 9,      /* ls_poll: unknown or already collected ticket                   */
+  LS_EUNSUPPORTED = 10   /* grid size with no FFT length implemented (2n must be 16..384) */
+};
+
+typedef struct { int nx, ny, nz; } ls_grid;      /* voxels per axis, each in {8,12,16,24,32,48,64,96,128,192} */
+typedef struct { float re, im; } ls_c64;
+
+typedef struct {
+  double tol;          /* BiCGStab stop: ||r|| <= tol ||b|| (recursive residual).  Default 1e-6.      */
+  int max_iter;        /* iterations per view before LS_NOT_CONVERGED.  Default 1000.                 */
+  int oversample_p;    /* Green-spectrum oversampling p of Theorem 1 / Prop. 1 (even, >= 2).  Default 4 */
+  int det_mx, det_my;  /* detector pixels (0 = nx, ny); m <= n and n - m even (centred window).     */
+  double x_gamma;      /* detector plane position along z in micrometres; <= 0 means 3 L_z / 4.       */
+  int max_restarts;    /* restarts from the true residual when it misses 10 tol at exit.  Default 4.  */
+  int check_every;     /* iterations between host reads of the convergence mask (0 = auto).          */
+  int use_graphs;      /* 1 = replay the BiCGStab iteration from a captured CUDA graph.  Default 1.  */
+} ls_options;
+
+typedef struct {
+  int status;                 /* LS_OK, LS_NOT_CONVERGED or LS_BREAKDOWN                         */
+  int iterations;             /* BiCGStab iterations (each has two matvecs)                      */
+  int restarts;               /* restarts from the true residual                                 */
+  int matvecs;                /* operator applications including residual checks                 */
+  double rel_residual;        /* recursive ||r|| / ||b|| at exit                                 */
+  double true_rel_residual;   /* recomputed ||b - A x|| / ||b|| at exit (float32 operator)       */
+} ls_stats;
+
+typedef struct ls_plan ls_plan;
+
+/* Fill *opt with the defaults listed above. */
+void ls_default_options(ls_options* opt);
+
+/* Create a plan for one grid: voxel pitch `voxel` (um, = h of Theorem 1),
+ * background wavenumber k_b = 2 pi eta_b / lambda (1/um, Sec. 2.1).
+ * `padding` is the storage padding of Prop. 1 and must be 2.  Builds the
+ * Green spectrum with opt->oversample_p (see ls_green_spectrum) and the
+ * far-field kernels (Sec. 3.2).  Requires k_b h < pi (Theorem 1).  *out
+ * receives the plan, to be released with ls_plan_destroy.  Errors:
+ * LS_EINVAL, LS_EUNSUPPORTED, LS_ENOMEM, LS_ECUDA. */
+int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel,
+                   const ls_options* opt, ls_plan** out);
+void ls_plan_destroy(ls_plan* plan);
+
+/* (Re)build the Green spectrum Ghat = F_{2n}(g_t^m) of Prop. 1 for
+ * oversampling p (even >= 2): ghat_t of eq. GreenL/GreenL2 sampled at
+ * delta ((p/2) q - s), (p/2)^3 inverse FFTs of size (2n)^3, phase-shifted sum,
+ * kernel zeroed at the Nyquist offset, forward FFT -- all in float64 on the
+ * GPU, then stored as complex64 (one octant, Ghat is even in every axis).
+ * If out_full != NULL it receives the full spectrum, (2nz)(2ny)(2nx) ls_c64,
+ * unnormalised (the same array as F_{2n} of the kernel).  Synchronous. */
+int ls_green_spectrum(ls_plan* plan, int oversample_p, ls_c64* out_full, void* cuda_stream);
+
+/* Scattering potential f = k_b^2 ((eta_b + dn)^2 / eta_b^2 - 1) (Sec. 2.1)
+ * for `count` voxels: dn (device float32 contrast) -> f (device float32). */
+int ls_scattering_potential(const float* dn, size_t count, double eta_b, double k_b,
+                            float* f, void* cuda_stream);
+
+/* Incident plane waves u_in,q(x) = exp(i k_q . x) at the voxel centres
+ * (Fig. 1).  kvec: host array of 3 * n_views doubles (kx, ky, kz per view,
+ * 1/um).  u_in[q]: device, N complex64 each. */
+int ls_plane_waves(ls_plan* plan, int n_views, const double* kvec,
+                   ls_c64* const* u_in, void* cuda_stream);
+
+/* out = G v (adjoint != 0: G^H v), Theorem 1 with Prop. 1's kernel.  v, out: N complex64. */
+int ls_apply_green(ls_plan* plan, const ls_c64* v, ls_c64* out, int adjoint, void* cuda_stream);
+
+/* y = x - G (f .* x) (adjoint != 0: x - G^H (f .* x)), the operator of eq. lipp1. */
+int ls_matvec(ls_plan* plan, const float* f, const ls_c64* x, ls_c64* y, int adjoint,
+              void* cuda_stream);
+
+/* Forward model for n_views illuminations of one potential f (eqs. lipp1, lipp2):
+ * BiCGStab on (I - G diag f) u = u_in[q] from u = u_in[q], all views batched,
+ * then the far field y_q = G~ (f .* u_q) on the detector.  u_out[q] (N) and
+ * far[q] (my*mx) may each be NULL (u_out == NULL: fields not returned;
+ * far == NULL: far field skipped).  stats: host array of n_views or NULL.
+ * Returns LS_OK, LS_NOT_CONVERGED or LS_BREAKDOWN (worst view), or an error. */
+int ls_forward(ls_plan* plan, const float* f, int n_views, const ls_c64* const* u_in,
+               ls_c64* const* u_out, ls_c64* const* far, ls_stats* stats, void* cuda_stream);
+
+/* far[q] = G~ (f .* u[q]) (eq. Gtild-1, midpoint rule, exact per-slice 2-D convolutions). */
+int ls_farfield(ls_plan* plan, const float* f, int n_views, const ls_c64* const* u,
+                ls_c64* const* far, void* cuda_stream);
+
+/* out[q] = G~^H r[q]: r[q] is my*mx, out[q] is N. */
+int ls_farfield_adjoint(ls_plan* plan, int n_views, const ls_c64* const* r,
+                        ls_c64* const* out, void* cuda_stream);
+
+/* res[q] = pred[q] - meas[q] over `count` complex entries per view, and
+ * loss_out[q] (host, may be NULL) = ||res[q]||^2 accumulated in float64. */
+int ls_residual(int n_views, size_t count, const ls_c64* const* pred, const ls_c64* const* meas,
+                ls_c64* const* res, double* loss_out, void* cuda_stream);
+
+/* Data-fidelity gradient (Alg. 1 line 6, Jacobian adjoint):
+ *   grad = sum_q c_q Re(conj(u_q) .* w_q),  (I - G^H diag f) w_q = G~^H r_q,
+ * with r_q = residuals[q] (my*mx, e.g. H_q(f) - y_q) and c_q = view_weights[q]
+ * (host array; NULL means 1).  u_fwd[q] are the forward fields (checkpoint); if
+ * u_fwd == NULL they are recomputed from u_in (u_in is ignored otherwise).
+ * grad: N float32, overwritten.  stats: host array of n_views (adjoint solves) or NULL. */
+int ls_gradient(ls_plan* plan, const float* f, int n_views, const ls_c64* const* u_in,
+                const ls_c64* const* u_fwd, const ls_c64* const* residuals,
+                const double* view_weights, float* grad, ls_stats* stats, void* cuda_stream);
+
+/* ---------------------------------------------------------------- serving */
+
+enum ls_request_kind { LS_REQ_FORWARD = 0, LS_REQ_GRADIENT = 1 };
+
+typedef struct {
+  size_t hbm_budget_bytes;   /* device memory the server may use for plans and Krylov state (0 = 80% of free) */
+  int max_views_per_grid;    /* cap of concurrently resident views per grid size (0 = no cap)                  */
+  double tol;                /* solver tolerance (0 = 1e-6)                                                     */
+  int max_iter;              /* 0 = 1000                                                                        */
+  double k_b, voxel;         /* optics shared by all requests (1/um, um)                                        */
+} ls_server_options;
+
+typedef struct {
+  int kind;                  /* LS_REQ_FORWARD or LS_REQ_GRADIENT                                   */
+  ls_grid grid;              /* voxel counts                                                        */
+  int n_views;
+  const float* f;            /* device, N; must stay valid until ls_poll returns a final status     */
+  const double* kvec;        /* host, 3*n_views plane-wave vectors (copied by ls_submit)            */
+  const ls_c64* meas;        /* GRADIENT: device [n_views][my*mx] measurements y_q                   */
+  ls_c64* u_out;             /* device [n_views][N] or NULL                                         */
+  ls_c64* far;               /* device [n_views][my*mx] or NULL (FORWARD)                            */
+  float* grad;               /* GRADIENT: device N, gradient of sum_q ||H_q - y_q||^2/(2||y_q||^2) */
+  double* loss;              /* GRADIENT: host double receiving the loss, or NULL                    */
+} ls_request;
+
+typedef struct {
+  int status;                /* final status of the request (LS_OK, LS_NOT_CONVERGED, ...)         */
+  int iterations_max;        /* largest BiCGStab iteration count over the request's views          */
+  double submit_to_done_ms;  /* wall time from ls_submit to completion                             */
+} ls_result;
+
+typedef struct ls_server ls_server;
+
+/* Start a server thread that runs continuous batching: requests of the same
+ * grid share one batched BiCGStab engine; new requests join at iteration
+ * boundaries as slots and device memory free up. */
+int ls_server_create(const ls_server_options* opt, ls_server** out);
+/* Queue a request (copied; device buffers are referenced).  *ticket identifies it.
+ * LS_EAGAIN if it can never fit the HBM budget, LS_EINVAL on bad arguments. */
+int ls_submit(ls_server* srv, const ls_request* req, uint64_t* ticket);
+/* LS_PENDING while running; otherwise the final status (also in res) and the
+ * ticket is released.  res may be NULL. */
+int ls_poll(ls_server* srv, uint64_t ticket, ls_result* res);
+/* Stops the server thread after the queued work and frees its memory. */
+void ls_server_destroy(ls_server* srv);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Kernel kinds timed by ls_profile (the five FFT passes of one operator
+ * application, the BiCGStab update and scalar steps, far-field kernels). */
+enum ls_kernel_kind {
+  LS_K_FX = 0, LS_K_FY = 1, LS_K_Z = 2, LS_K_IY = 3, LS_K_IX = 4,
+  LS_K_UPDATE = 5, LS_K_SCALAR = 6, LS_K_FAR = 7, LS_K_OTHER = 8, LS_K_COUNT = 9
+};
+
+typedef struct {
+  double ms[LS_K_COUNT];          /* summed device time per kind (CUDA events around each launch) */
+  long long launches[LS_K_COUNT]; /* launches per kind                                            */
+  long long slot_passes[LS_K_COUNT]; /* sum over launches of the slots each launch covered        */
+} ls_kernel_times;
+
+/* enable = 1: reset the counters and time every kernel launch of this plan
+ * with a CUDA event pair on the launching stream (graph replay is disabled
+ * while profiling so each launch can be bracketed).  enable = 0: stop.
+ * out (host, may be NULL) receives the totals so far (synchronises the plan's
+ * pending events).  Adds no work to the kernels themselves. */
+int ls_profile(ls_plan* plan, int enable, ls_kernel_times* out);
+
+/* ---------------------------------------------------------------- misc */
+
+const char* ls_status_string(int status);
+const char* ls_last_error(void);
+/* Device memory (bytes) a plan for this grid and n_views views needs at steady state. */
+size_t ls_workspace_bytes(const ls_grid* grid, int n_views);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LS_H */

@@ -1,0 +1,276 @@
+"""GB300 Lippmann-Schwinger forward model and gradient (arXiv 1910.13844).
+
+Thin Python binding of the C ABI in ``include/ls.h``: every function here has
+the C name, marshals torch tensors (device memory) and Python lists into
+pointers, and calls the CUDA library ``libls.so``.  All arithmetic runs in the
+library's kernels; if the library is missing the import fails.
+
+Volumes are torch tensors of shape (nz, ny, nx): complex64 fields, float32
+potentials.  Detector arrays are (my, mx) complex64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import (LS_BREAKDOWN, LS_EAGAIN, LS_ECUDA, LS_EINVAL, LS_ENOMEM, LS_ENOTFOUND, LS_EUNSUPPORTED,
+                   LS_NOT_CONVERGED, LS_OK, LS_PENDING, LS_REQ_FORWARD, LS_REQ_GRADIENT, LS_TIMEOUT, ls_grid,
+                   ls_options, ls_request, ls_result, ls_server_options, ls_stats)
+
+_lib = _abi.load()
+
+__all__ = [
+    "LsError", "Plan", "ls_default_options", "ls_plan_create", "ls_plan_destroy", "ls_green_spectrum",
+    "ls_scattering_potential", "ls_plane_waves", "ls_apply_green", "ls_matvec", "ls_forward", "ls_farfield",
+    "ls_farfield_adjoint", "ls_residual", "ls_gradient", "ls_server_create", "ls_submit", "ls_poll",
+    "ls_server_destroy", "ls_status_string", "ls_last_error", "ls_workspace_bytes", "ls_profile", "library_path",
+]
+
+_SOFT = (LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN, LS_TIMEOUT, LS_PENDING)
+
+
+class LsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib.ls_status_string(code).decode()
+        detail = _lib.ls_last_error().decode()
+        super().__init__(f"{where}: {msg} ({detail})")
+
+
+def _check(code: int, where: str) -> int:
+    if code not in _SOFT:
+        raise LsError(code, where)
+    return code
+
+
+def library_path() -> str:
+    return _abi.LIB_PATH
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, torch.Tensor):
+        if not t.is_cuda:
+            raise ValueError("tensor must be on a CUDA device")
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return t.data_ptr()
+    raise TypeError(f"expected a CUDA tensor or an integer device pointer, got {type(t)}")
+
+
+def _views(ts):
+    """Host array of device pointers for a list of tensors / a [Q, ...] tensor, or None."""
+    if ts is None:
+        return None, 0
+    if isinstance(ts, torch.Tensor):
+        ts = list(ts.unbind(0)) if ts.dim() >= 2 and ts.is_contiguous() else [ts]
+    ptrs = [_ptr(t) for t in ts]
+    arr = (C.c_void_p * len(ptrs))(*ptrs)
+    return arr, len(ptrs)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def ls_status_string(code: int) -> str:
+    return _lib.ls_status_string(int(code)).decode()
+
+
+def ls_last_error() -> str:
+    return _lib.ls_last_error().decode()
+
+
+def ls_default_options(**overrides) -> ls_options:
+    o = ls_options()
+    _lib.ls_default_options(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def ls_workspace_bytes(grid, n_views: int) -> int:
+    g = ls_grid(*grid)
+    return int(_lib.ls_workspace_bytes(C.byref(g), int(n_views)))
+
+
+def ls_plan_create(grid, padding: int, k_b: float, voxel: float, opt: ls_options | None = None) -> int:
+    """grid = (nx, ny, nz).  Returns the plan handle (int)."""
+    g = ls_grid(*[int(v) for v in grid])
+    out = C.c_void_p()
+    _check(_lib.ls_plan_create(C.byref(g), int(padding), float(k_b), float(voxel),
+                               C.byref(opt) if opt is not None else None, C.byref(out)), "ls_plan_create")
+    return out.value
+
+
+def ls_plan_destroy(plan: int) -> None:
+    _lib.ls_plan_destroy(plan)
+
+
+def ls_green_spectrum(plan: int, oversample_p: int, out=None, stream=None) -> int:
+    return _check(_lib.ls_green_spectrum(plan, int(oversample_p), _ptr(out), _stream(stream)), "ls_green_spectrum")
+
+
+def ls_scattering_potential(dn, eta_b: float, k_b: float, f, stream=None) -> int:
+    return _check(_lib.ls_scattering_potential(_ptr(dn), dn.numel(), float(eta_b), float(k_b), _ptr(f),
+                                               _stream(stream)), "ls_scattering_potential")
+
+
+def ls_plane_waves(plan: int, kvec, u_in, stream=None) -> int:
+    k = np.ascontiguousarray(np.asarray(kvec, dtype=np.float64).reshape(-1, 3))
+    arr, n = _views(u_in)
+    if n != k.shape[0]:
+        raise ValueError("one wave vector per view")
+    return _check(_lib.ls_plane_waves(plan, n, k.ctypes.data_as(C.POINTER(C.c_double)), arr, _stream(stream)),
+                  "ls_plane_waves")
+
+
+def ls_apply_green(plan: int, v, out, adjoint: bool = False, stream=None) -> int:
+    return _check(_lib.ls_apply_green(plan, _ptr(v), _ptr(out), int(bool(adjoint)), _stream(stream)),
+                  "ls_apply_green")
+
+
+def ls_matvec(plan: int, f, x, y, adjoint: bool = False, stream=None) -> int:
+    return _check(_lib.ls_matvec(plan, _ptr(f), _ptr(x), _ptr(y), int(bool(adjoint)), _stream(stream)), "ls_matvec")
+
+
+def ls_forward(plan: int, f, u_in, u_out=None, far=None, stream=None):
+    """Returns (status, [stats dict per view])."""
+    a_in, n = _views(u_in)
+    a_out, _ = _views(u_out)
+    a_far, _ = _views(far)
+    st = (ls_stats * n)()
+    code = _check(_lib.ls_forward(plan, _ptr(f), n, a_in, a_out, a_far, st, _stream(stream)), "ls_forward")
+    return code, [s.as_dict() for s in st]
+
+
+def ls_farfield(plan: int, f, u, far, stream=None) -> int:
+    a_u, n = _views(u)
+    a_far, _ = _views(far)
+    return _check(_lib.ls_farfield(plan, _ptr(f), n, a_u, a_far, _stream(stream)), "ls_farfield")
+
+
+def ls_farfield_adjoint(plan: int, r, out, stream=None) -> int:
+    a_r, n = _views(r)
+    a_o, _ = _views(out)
+    return _check(_lib.ls_farfield_adjoint(plan, n, a_r, a_o, _stream(stream)), "ls_farfield_adjoint")
+
+
+def ls_residual(pred, meas, res, stream=None):
+    """res = pred - meas per view; returns per-view ||res||^2 (float64 numpy array)."""
+    a_p, n = _views(pred)
+    a_m, _ = _views(meas)
+    a_r, _ = _views(res)
+    count = (pred[0] if isinstance(pred, (list, tuple)) else pred[0]).numel()
+    loss = (C.c_double * n)()
+    _check(_lib.ls_residual(n, count, a_p, a_m, a_r, loss, _stream(stream)), "ls_residual")
+    return np.array(loss[:], dtype=np.float64)
+
+
+def ls_gradient(plan: int, f, residuals, grad, u_in=None, u_fwd=None, view_weights=None, stream=None):
+    """Returns (status, [stats dict per view]) and writes grad."""
+    a_r, n = _views(residuals)
+    a_in, _ = _views(u_in)
+    a_fw, _ = _views(u_fwd)
+    w = None
+    if view_weights is not None:
+        w = (C.c_double * n)(*[float(x) for x in view_weights])
+    st = (ls_stats * n)()
+    code = _check(_lib.ls_gradient(plan, _ptr(f), n, a_in, a_fw, a_r, w, _ptr(grad), st, _stream(stream)),
+                  "ls_gradient")
+    return code, [s.as_dict() for s in st]
+
+
+def ls_profile(plan: int, enable: bool):
+    """Turn per-launch event timing on/off; returns {kind: (ms, launches, slot_passes)} so far."""
+    t = _abi.ls_kernel_times()
+    _check(_lib.ls_profile(plan, int(bool(enable)), C.byref(t)), "ls_profile")
+    return {name: (t.ms[i], t.launches[i], t.slot_passes[i]) for i, name in enumerate(_abi.LS_K_NAMES)}
+
+
+def ls_server_create(opt: ls_server_options) -> int:
+    out = C.c_void_p()
+    _check(_lib.ls_server_create(C.byref(opt), C.byref(out)), "ls_server_create")
+    return out.value
+
+
+def ls_submit(server: int, req: ls_request) -> tuple[int, int]:
+    t = C.c_uint64()
+    code = _lib.ls_submit(server, C.byref(req), C.byref(t))
+    if code not in (LS_OK, LS_EAGAIN):
+        raise LsError(code, "ls_submit")
+    return code, t.value
+
+
+def ls_poll(server: int, ticket: int):
+    r = ls_result()
+    code = _lib.ls_poll(server, C.c_uint64(ticket), C.byref(r))
+    if code == LS_ENOTFOUND:
+        raise LsError(code, "ls_poll")
+    return code, {"status": r.status, "iterations_max": r.iterations_max, "ms": r.submit_to_done_ms}
+
+
+def ls_server_destroy(server: int) -> None:
+    _lib.ls_server_destroy(server)
+
+
+class Plan:
+    """Owning wrapper of an ls_plan for one grid (shape given as (nz, ny, nx))."""
+
+    def __init__(self, shape, k_b: float, voxel: float, **options):
+        self.shape = tuple(int(s) for s in shape)
+        nz, ny, nx = self.shape
+        self.k_b = float(k_b)
+        self.voxel = float(voxel)
+        self.options = ls_default_options(**options)
+        self.handle = ls_plan_create((nx, ny, nz), 2, k_b, voxel, self.options)
+        self.det = (self.options.det_my or ny, self.options.det_mx or nx)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ls_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # convenience allocations
+    def field(self, n=None, device="cuda"):
+        s = self.shape if n is None else (n,) + self.shape
+        return torch.empty(s, dtype=torch.complex64, device=device)
+
+    def detector(self, n=None, device="cuda"):
+        s = self.det if n is None else (n,) + self.det
+        return torch.empty(s, dtype=torch.complex64, device=device)
+
+    def plane_waves(self, kvec, stream=None):
+        k = np.asarray(kvec, dtype=np.float64).reshape(-1, 3)
+        u = self.field(k.shape[0])
+        ls_plane_waves(self.handle, k, u, stream)
+        return u
+
+    def forward(self, f, u_in, want_fields=True, want_far=True, stream=None):
+        q = u_in.shape[0]
+        u = self.field(q) if want_fields else None
+        far = self.detector(q) if want_far else None
+        code, stats = ls_forward(self.handle, f, u_in, u, far, stream)
+        return u, far, code, stats
+
+    def gradient(self, f, residuals, u_fwd=None, u_in=None, weights=None, stream=None):
+        g = torch.empty(self.shape, dtype=torch.float32, device=f.device)
+        code, stats = ls_gradient(self.handle, f, residuals, g, u_in=u_in, u_fwd=u_fwd, view_weights=weights,
+                                  stream=stream)
+        return g, code, stats

@@ -1,0 +1,104 @@
+// Host-side plan and batched solver engine shared by the C ABI and the server.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "green.cuh"
+#include "krylov.cuh"
+#include "passes.cuh"
+
+namespace lsgpu {
+
+enum Vec : int { V_B = 0, V_X = 1, V_R = 2, V_RH = 3, V_P = 4, V_V = 5, V_S = 6, V_T = 7, NVEC = 8 };
+
+struct Engine {
+  int cap = 0;                  // slots allocated
+  size_t N = 0;
+  float2* vec = nullptr;        // [NVEC][cap][N]
+  float2* a1 = nullptr;         // [cap][nz][ny][2nx]
+  float2* a2 = nullptr;         // [cap][nz][2ny][2nx]
+  size_t a1_stride = 0, a2_stride = 0;
+  float2* far = nullptr;        // [cap][my*mx]
+  float2* ucache = nullptr;     // [cap][N] forward fields kept for a gradient (lazy)
+  int ucache_cap = 0;
+  double* partials = nullptr;   // [cap][maxparts][4]
+  int maxparts = 0;
+  SlotDev* slots_d = nullptr;
+  SlotDev* slots_h = nullptr;   // pinned mirror
+  int* counts_d = nullptr;
+  int* counts_h = nullptr;      // pinned
+  void** ptrs_d = nullptr;      // pointer tables: [4][cap]
+  double* kvec_d = nullptr;     // [cap*3]
+  float* weights_d = nullptr;   // [cap]
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t iter_graph = nullptr;
+  int iter_graph_slots = 0;
+  float2* vptr(int v, int slot = 0) const { return vec + ((size_t)v * cap + slot) * N; }
+};
+
+struct Profiler {
+  bool on = false;
+  struct Pending { int kind; int slots; cudaEvent_t a, b; };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pending> pending;
+  double ms[LS_K_COUNT] = {};
+  long long launches[LS_K_COUNT] = {};
+  long long slot_passes[LS_K_COUNT] = {};
+};
+
+}  // namespace lsgpu
+
+struct ls_plan {
+  int nx = 0, ny = 0, nz = 0;
+  size_t N = 0;
+  double kb = 0, h = 0;
+  ls_options opt{};
+  int mx = 0, my = 0, ox = 0, oy = 0;
+  double x_gamma = 0;
+  lsgpu::PassLaunch px{}, py{}, pz{};
+  float2 *tw_x = nullptr, *tw2_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
+  float2* gocta = nullptr;
+  float2* k2hat = nullptr;
+  int p_built = 0;
+  lsgpu::Engine eng;
+  lsgpu::Profiler prof;
+};
+
+namespace lsgpu {
+
+int engine_reserve(ls_plan* P, int nslots);
+int engine_reserve_ucache(ls_plan* P, int nslots);
+void engine_release(Engine& e);
+
+// Upload host slot states [0, nslots) and run BiCGStab until every slot has
+// left SLOT_ITER/SLOT_RESID.  Vectors b and x must be set.
+int engine_solve(ls_plan* P, int nslots, cudaStream_t st);
+// Sequences of kernel launches (no synchronisation).
+void seq_resid(ls_plan* P, int nslots, cudaStream_t st);
+void seq_iter(ls_plan* P, int nslots, cudaStream_t st);
+void seq_far(ls_plan* P, int nslots, unsigned mask, cudaStream_t st);
+void seq_far_adjoint(ls_plan* P, int nslots, const float2* const* r_dev_table, unsigned mask, cudaStream_t st);
+int engine_upload_ptrs(ls_plan* P, int table, const void* const* host_ptrs, int n, cudaStream_t st);
+void** engine_ptr_table(ls_plan* P, int table);
+void slot_defaults(const ls_plan* P, SlotDev& s, const float* f, int adjoint);
+
+// Launch wrapper: when profiling is on, bracket the launch with an event pair.
+cudaEvent_t prof_event(ls_plan* P);
+void prof_resolve(ls_plan* P, bool wait);
+template <class F>
+inline void timed(ls_plan* P, int kind, int nslots, cudaStream_t st, F&& launch) {
+  if (!P->prof.on) {
+    launch();
+    return;
+  }
+  cudaEvent_t a = prof_event(P), b = prof_event(P);
+  cudaEventRecord(a, st);
+  launch();
+  cudaEventRecord(b, st);
+  P->prof.pending.push_back({kind, nslots, a, b});
+}
+
+}  // namespace lsgpu

@@ -1,0 +1,507 @@
+// Pencil FFT passes of the zero-padded Green convolution (Theorem 1 with the
+// twofold padding of Prop. 1), with the BiCGStab vector updates fused into the
+// first and last passes.
+//
+// One matvec y = x - G (f x) on an nx*ny*nz grid is five passes, each one
+// kernel, over complex64 arrays in HBM:
+//   FX  rows (z,y):   f*x, zero-pad x -> 2nx, FFT along x      [nz][ny][nx]   -> A1 [nz][ny][2nx]
+//   FY  pencils (z,kx): zero-pad y, FFT along y                 A1             -> A2 [nz][2ny][2nx]
+//   Z   pencils (ky,kx): zero-pad z, FFT, * Ghat, IFFT, crop z  A2 in place (first nz planes)
+//   IY  pencils (z,kx): IFFT along y, crop y                    A2             -> A1
+//   IX  rows (z,y):   IFFT along x, crop x, epilogue            A1             -> [nz][ny][nx]
+// The inverse normalisation 1/(8 nx ny nz) is folded into Ghat.
+//
+// Each length-L transform (L = 2n) is split L = R1 * R2 and done by T = max(R1, R2)
+// threads per pencil in two register stages with one shared-memory exchange:
+//   X[k1 + R1 k2] = sum_n2 W_R2^{n2 k2} W_L^{n2 k1} sum_n1 x[R2 n1 + n2] W_R1^{n1 k1}.
+// Zero padding means the stage-1 inputs with n1 >= R1/2 vanish; cropping means
+// stage 2 only produces k2 < R2/2.  The z pass chains forward stage 2, the
+// Green multiply and inverse stage 1 in registers (the inverse uses the
+// transposed split), so it needs two exchanges for a forward+inverse pair.
+#pragma once
+
+#include "common.cuh"
+#include "dft.cuh"
+
+namespace lsgpu {
+
+enum FxMode : int { FX_F_TIMES = 0, FX_COPY = 1, FX_BICG_P = 2, FX_BICG_S = 3 };
+enum IxMode : int { IX_STORE = 0, IX_MATVEC = 1, IX_BICG_V = 2, IX_BICG_T = 3, IX_RESID = 4 };
+
+struct SlotSel {
+  const SlotDev* slots;   // null: every slot runs with the defaults below
+  unsigned mask;          // run slot s iff (slots[s].flags & mask) != 0 (mask 0: all)
+  const float* f_default; // potential when slots == null
+  int adj_default;        // adjoint flag when slots == null
+};
+
+struct FxParams {
+  SlotSel sel;
+  int nx, rows;                // transform length is 2nx; rows = ny*nz pencils per slot
+  int mode;
+  const float2* src;           // F_TIMES/COPY: vector; BICG_P/BICG_S: r
+  float2* vp;                  // BICG_P: p (read, then overwritten with the new p)
+  const float2* vv;            // BICG_P/BICG_S: v
+  float2* vs;                  // BICG_S: s (written)
+  size_t vstride;              // elements between slots for src/vp/vv/vs and f (f is shared unless slots)
+  float2* dst;                 // [rows][2nx]
+  size_t dst_stride;
+  const float2* tw2;           // tw2[k1*R2 + n2] = exp(-2 pi i n2 k1 / L)
+};
+
+struct StridedParams {
+  SlotSel sel;
+  int ncont;                   // contiguous length of a row (2nx); the strided axis has length L
+  int planes;                  // number of independent planes (nz for FY/IY)
+  int out_o, out_m;            // IY: output window [out_o, out_o + out_m) of the cropped axis
+  const float2* src; size_t src_stride;
+  float2* dst; size_t dst_stride;
+  size_t src_plane, dst_plane; // elements between planes
+  const float2* tw;            // tw[j] = exp(-2 pi i j / L)
+};
+
+struct ZParams {
+  SlotSel sel;
+  int nx, ny, nz;              // A2 is [nz][2ny][2nx]
+  float2* a2; size_t a2_stride;
+  const float2* gocta;         // [(nz+1)][(ny+1)][(nx+1)], scaled by 1/(8 nx ny nz)
+  const float2* tw;
+};
+
+struct IxParams {
+  SlotSel sel;
+  int nx, rows;                // input rows of length 2nx; output rows of length nx (or window)
+  int mode;
+  const float2* src; size_t src_stride;   // A1
+  const float2* in0;           // MATVEC: x; BICG_V: p; BICG_T: s; RESID: x
+  const float2* in1;           // BICG_V: rh; RESID: b
+  float2* out0;                // STORE/MATVEC: y; BICG_V: v; BICG_T: t; RESID: r
+  float2* out1;                // RESID: rh (= r)
+  size_t vstride;              // slot stride for in*/out* (STORE: stride of out0)
+  int out_o, out_m;            // STORE: output window [out_o, out_o+out_m) of x; out rows are out_m long
+  double* partials;            // [slot][gridDim.x][4]
+  const float2* tw2;
+};
+
+__device__ __forceinline__ bool slot_runs(const SlotSel& s, int slot) {
+  return !(s.slots && s.mask && !(s.slots[slot].flags & s.mask));
+}
+__device__ __forceinline__ const float* slot_f(const SlotSel& s, int slot) {
+  return s.slots ? s.slots[slot].f : s.f_default;
+}
+__device__ __forceinline__ int slot_adj(const SlotSel& s, int slot) {
+  return s.slots ? s.slots[slot].adjoint : s.adj_default;
+}
+
+__host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
+
+template <int L> struct Radix;
+template <> struct Radix<16>  { static constexpr int R1 = 4,  R2 = 4;  };
+template <> struct Radix<24>  { static constexpr int R1 = 4,  R2 = 6;  };
+template <> struct Radix<32>  { static constexpr int R1 = 8,  R2 = 4;  };
+template <> struct Radix<48>  { static constexpr int R1 = 8,  R2 = 6;  };
+template <> struct Radix<64>  { static constexpr int R1 = 8,  R2 = 8;  };
+template <> struct Radix<96>  { static constexpr int R1 = 8,  R2 = 12; };
+template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8;  };
+template <> struct Radix<192> { static constexpr int R1 = 16, R2 = 12; };
+template <> struct Radix<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct Radix<384> { static constexpr int R1 = 16, R2 = 24; };
+
+template <int L>
+struct Geo {
+  static constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2;
+  static constexpr int T = imax(R1, R2);
+  static constexpr int PC = (256 / T) > 0 ? (256 / T) : 1;   // rows per CTA, contiguous passes
+  static constexpr int PS = 16;                              // pencils per CTA, strided passes
+  static constexpr int SROW = R2 + 1;                        // padded row of the contiguous exchange
+  static constexpr size_t smem_contig = (size_t)PC * R1 * SROW * sizeof(float2);
+  static constexpr size_t smem_strided = (size_t)L * PS * sizeof(float2);
+};
+
+// Warp-then-block reduction of NV float partial sums; thread 0 writes doubles to out[0..NV).
+template <int NV>
+__device__ __forceinline__ void block_sum_store(float (&acc)[NV], double* out) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+  __shared__ double wsum[32][NV];
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  const int lane = tid & 31, w = tid >> 5, nw = (nthreads + 31) >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) wsum[w][j] = (double)acc[j];
+  __syncthreads();
+  if (w == 0) {
+    double v[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = lane < nw ? wsum[lane][j] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    if (lane == 0)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) out[j] = v[j];
+  }
+}
+
+// ------------------------------------------------------------------------- FX
+template <int L>
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC) k_fx(FxParams a) {
+  using G = Geo<L>;
+  constexpr int R1 = G::R1, R2 = G::R2;
+  extern __shared__ float2 sm[];
+  const int slot = blockIdx.y;
+  if (!slot_runs(a.sel, slot)) return;
+  const int t = threadIdx.x, p = threadIdx.y;
+  const int nx = L / 2;
+  const int row = blockIdx.x * G::PC + p;
+  const bool valid = row < a.rows;
+  const size_t voff = (size_t)slot * a.vstride + (size_t)row * nx;
+  const float* f = slot_f(a.sel, slot);
+  float2 v[R1];
+#pragma unroll
+  for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+  if (valid && t < R2) {
+    float fa = 1.f, fb = 0.f, al_re = 0.f, al_im = 0.f, om_re = 0.f, om_im = 0.f;
+    bool first = false;
+    if (a.mode == FX_BICG_P) {
+      const SlotDev& sd = a.sel.slots[slot];
+      first = sd.first != 0;
+      fa = (float)sd.beta.x; fb = (float)sd.beta.y;
+      om_re = (float)sd.omega.x; om_im = (float)sd.omega.y;
+    } else if (a.mode == FX_BICG_S) {
+      const SlotDev& sd = a.sel.slots[slot];
+      al_re = (float)sd.alpha.x; al_im = (float)sd.alpha.y;
+    }
+#pragma unroll
+    for (int n1 = 0; n1 < R1 / 2; ++n1) {
+      const int x = R2 * n1 + t;
+      const size_t i = voff + x;
+      float2 val = __ldg(a.src + i);
+      if (a.mode == FX_BICG_P) {
+        if (!first) {
+          // p = r + beta (p - omega v)
+          float2 pv = a.vp[i], vv = __ldg(a.vv + i);
+          float2 d = csub(pv, cmul(make_float2(om_re, om_im), vv));
+          val = cadd(val, cmul(make_float2(fa, fb), d));
+        }
+        a.vp[i] = val;
+      } else if (a.mode == FX_BICG_S) {
+        // s = r - alpha v
+        float2 vv = __ldg(a.vv + i);
+        val = csub(val, cmul(make_float2(al_re, al_im), vv));
+        a.vs[i] = val;
+      }
+      if (a.mode != FX_COPY) {
+        const float fv = __ldg(f + (size_t)row * nx + x);
+        val = cscale(val, fv);
+      }
+      v[n1] = val;
+    }
+  }
+  float2* S = sm + (size_t)p * R1 * G::SROW;
+  if (t < R2) {
+    Dft<R1, -1>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], __ldg(a.tw2 + k1 * R2 + t));
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) S[k1 * G::SROW + t] = v[k1];
+  }
+  __syncthreads();
+  if (valid && t < R1) {
+    float2 u[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = S[t * G::SROW + n2];
+    Dft<R2, -1>::run(u);
+    float2* d = a.dst + (size_t)slot * a.dst_stride + (size_t)row * L;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) d[t + R1 * k2] = u[k2];
+  }
+}
+
+// ------------------------------------------------------------------------- FY / IY
+// Pencils along a strided axis; tile = 16 consecutive entries of the contiguous axis.
+template <int L, int DIR>
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_strided(StridedParams a) {
+  using G = Geo<L>;
+  constexpr int R1 = G::R1, R2 = G::R2, P = G::PS;
+  extern __shared__ float2 sm[];
+  const int slot = blockIdx.y;
+  if (!slot_runs(a.sel, slot)) return;
+  const int p = threadIdx.x, t = threadIdx.y;
+  const int tiles_c = (a.ncont + P - 1) / P;
+  const int plane = blockIdx.x / tiles_c;
+  const int c = (blockIdx.x % tiles_c) * P + p;
+  const bool valid = c < a.ncont;
+  const float2* src = a.src + (size_t)slot * a.src_stride + (size_t)plane * a.src_plane + c;
+  float2 v[R1];
+#pragma unroll
+  for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+  if (valid && t < R2) {
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const int y = R2 * n1 + t;
+      if (DIR < 0 ? (n1 < R1 / 2) : true) v[n1] = __ldg(src + (size_t)y * a.ncont);
+    }
+  }
+  if (t < R2) {
+    Dft<R1, DIR>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+      float2 w = __ldg(a.tw + k1 * t);
+      v[k1] = DIR < 0 ? cmul(v[k1], w) : cmulc(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) sm[(k1 * R2 + t) * P + p] = v[k1];
+  }
+  __syncthreads();
+  if (valid && t < R1) {
+    float2 u[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = sm[(t * R2 + n2) * P + p];
+    Dft<R2, DIR>::run(u);
+    float2* dst = a.dst + (size_t)slot * a.dst_stride + (size_t)plane * a.dst_plane + c;
+    if (DIR < 0) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) dst[(size_t)(t + R1 * k2) * a.ncont] = u[k2];
+    } else {
+#pragma unroll
+      for (int k2 = 0; k2 < R2 / 2; ++k2) {
+        const int y = t + R1 * k2;
+        const int yo = y - a.out_o;
+        if (yo >= 0 && yo < a.out_m) dst[(size_t)yo * a.ncont] = u[k2];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------- Z
+template <int L>
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_z(ZParams a) {
+  using G = Geo<L>;
+  constexpr int R1 = G::R1, R2 = G::R2, P = G::PS;
+  extern __shared__ float2 sm[];
+  const int slot = blockIdx.y;
+  if (!slot_runs(a.sel, slot)) return;
+  const int p = threadIdx.x, t = threadIdx.y;
+  const int ncont = 2 * a.nx;
+  const int tiles_c = (ncont + P - 1) / P;
+  const int ky = blockIdx.x / tiles_c;
+  const int kx = (blockIdx.x % tiles_c) * P + p;
+  const bool valid = kx < ncont;
+  const size_t zstride = (size_t)(2 * a.ny) * ncont;
+  float2* col = a.a2 + (size_t)slot * a.a2_stride + (size_t)ky * ncont + kx;
+  // forward stage 1: inputs z = R2 n1 + t, n1 < R1/2 (z < nz)
+  float2 v[R1];
+#pragma unroll
+  for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+  if (valid && t < R2) {
+#pragma unroll
+    for (int n1 = 0; n1 < R1 / 2; ++n1) v[n1] = col[(size_t)(R2 * n1 + t) * zstride];
+  }
+  if (t < R2) {
+    Dft<R1, -1>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], __ldg(a.tw + k1 * t));
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) sm[(k1 * R2 + t) * P + p] = v[k1];
+  }
+  __syncthreads();
+  float2 u[R2];
+  if (t < R1) {
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = sm[(t * R2 + n2) * P + p];
+    Dft<R2, -1>::run(u);
+    // Green multiply: u[k2] holds kz = t + R1 k2; Ghat is even, read from one octant
+    const int fx = kx <= a.nx ? kx : ncont - kx;
+    const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
+    const float2* g = a.gocta + (size_t)fy * (a.nx + 1) + (valid ? fx : 0);
+    const size_t gz = (size_t)(a.ny + 1) * (a.nx + 1);
+    const bool adj = slot_adj(a.sel, slot) != 0;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int kz = t + R1 * k2;
+      const int fz = kz <= a.nz ? kz : 2 * a.nz - kz;
+      float2 gv = __ldg(g + (size_t)fz * gz);
+      u[k2] = adj ? cmulc(u[k2], gv) : cmul(u[k2], gv);
+    }
+    // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
+    Dft<R2, +1>::run(u);
+#pragma unroll
+    for (int j1 = 1; j1 < R2; ++j1) u[j1] = cmulc(u[j1], __ldg(a.tw + j1 * t));
+  }
+  __syncthreads();
+  if (t < R1) {
+#pragma unroll
+    for (int j1 = 0; j1 < R2; ++j1) sm[(j1 * R1 + t) * P + p] = u[j1];
+  }
+  __syncthreads();
+  if (valid && t < R2) {
+    float2 w[R1];
+#pragma unroll
+    for (int m2 = 0; m2 < R1; ++m2) w[m2] = sm[(t * R1 + m2) * P + p];
+    Dft<R1, +1>::run(w);
+    // outputs z = t + R2 j2, keep z < nz  (j2 < R1/2)
+#pragma unroll
+    for (int j2 = 0; j2 < R1 / 2; ++j2) col[(size_t)(t + R2 * j2) * zstride] = w[j2];
+  }
+}
+
+// ------------------------------------------------------------------------- IX
+template <int L>
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC) k_ix(IxParams a) {
+  using G = Geo<L>;
+  constexpr int R1 = G::R1, R2 = G::R2;
+  extern __shared__ float2 sm[];
+  const int slot = blockIdx.y;
+  if (!slot_runs(a.sel, slot)) return;
+  const int t = threadIdx.x, p = threadIdx.y;
+  const int nx = L / 2;
+  const int row = blockIdx.x * G::PC + p;
+  const bool valid = row < a.rows;
+  float2 v[R1];
+#pragma unroll
+  for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+  if (valid && t < R2) {
+    const float2* s = a.src + (size_t)slot * a.src_stride + (size_t)row * L;
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(s + R2 * n1 + t);
+  }
+  float2* S = sm + (size_t)p * R1 * G::SROW;
+  if (t < R2) {
+    Dft<R1, +1>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmulc(v[k1], __ldg(a.tw2 + k1 * R2 + t));
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) S[k1 * G::SROW + t] = v[k1];
+  }
+  __syncthreads();
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  if (valid && t < R1) {
+    float2 u[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = S[t * G::SROW + n2];
+    Dft<R2, +1>::run(u);
+    const size_t voff = (size_t)slot * a.vstride + (size_t)row * nx;
+#pragma unroll
+    for (int k2 = 0; k2 < R2 / 2; ++k2) {
+      const int x = t + R1 * k2;
+      const float2 g = u[k2];
+      const size_t i = voff + x;
+      switch (a.mode) {
+        case IX_STORE: {
+          const int xo = x - a.out_o;
+          if (xo >= 0 && xo < a.out_m) a.out0[(size_t)slot * a.vstride + (size_t)row * a.out_m + xo] = g;
+        } break;
+        case IX_MATVEC:
+          a.out0[i] = csub(__ldg(a.in0 + i), g);
+          break;
+        case IX_BICG_V: {
+          float2 vv = csub(__ldg(a.in0 + i), g);
+          a.out0[i] = vv;
+          float2 d = cdotterm(__ldg(a.in1 + i), vv);   // conj(rh) v
+          acc[0] += d.x; acc[1] += d.y;
+        } break;
+        case IX_BICG_T: {
+          float2 ss = __ldg(a.in0 + i);
+          float2 tt = csub(ss, g);
+          a.out0[i] = tt;
+          float2 d = cdotterm(tt, ss);                  // conj(t) s
+          acc[0] += d.x; acc[1] += d.y;
+          acc[2] += tt.x * tt.x + tt.y * tt.y;
+        } break;
+        case IX_RESID: {
+          float2 b = __ldg(a.in1 + i);
+          float2 r = cadd(csub(b, __ldg(a.in0 + i)), g);   // b - (x - G f x)
+          a.out0[i] = r;
+          a.out1[i] = r;
+          acc[0] += r.x * r.x + r.y * r.y;
+          acc[1] += b.x * b.x + b.y * b.y;
+        } break;
+      }
+    }
+  }
+  if (a.mode >= IX_BICG_V) {
+    block_sum_store<4>(acc, a.partials + ((size_t)slot * gridDim.x + blockIdx.x) * 4);
+  }
+}
+
+// ------------------------------------------------------------------------- launchers
+struct PassLaunch {
+  void (*fx)(const FxParams&, int nslots, cudaStream_t);
+  void (*fy)(const StridedParams&, int nslots, cudaStream_t);
+  void (*iy)(const StridedParams&, int nslots, cudaStream_t);
+  void (*z)(const ZParams&, int nslots, cudaStream_t);
+  void (*ix)(const IxParams&, int nslots, cudaStream_t);
+  int rows_per_cta_contig;
+  int pencils_per_cta_strided;
+};
+
+template <int L>
+struct PassImpl {
+  using G = Geo<L>;
+  static void fx(const FxParams& a, int nslots, cudaStream_t st) {
+    dim3 blk(G::T, G::PC), grd((a.rows + G::PC - 1) / G::PC, nslots);
+    k_fx<L><<<grd, blk, G::smem_contig, st>>>(a);
+  }
+  static void ix(const IxParams& a, int nslots, cudaStream_t st) {
+    dim3 blk(G::T, G::PC), grd((a.rows + G::PC - 1) / G::PC, nslots);
+    k_ix<L><<<grd, blk, G::smem_contig, st>>>(a);
+  }
+  static void fy(const StridedParams& a, int nslots, cudaStream_t st) {
+    dim3 blk(G::PS, G::T), grd(((a.ncont + G::PS - 1) / G::PS) * a.planes, nslots);
+    k_strided<L, -1><<<grd, blk, G::smem_strided, st>>>(a);
+  }
+  static void iy(const StridedParams& a, int nslots, cudaStream_t st) {
+    dim3 blk(G::PS, G::T), grd(((a.ncont + G::PS - 1) / G::PS) * a.planes, nslots);
+    k_strided<L, +1><<<grd, blk, G::smem_strided, st>>>(a);
+  }
+  static void z(const ZParams& a, int nslots, cudaStream_t st) {
+    dim3 blk(G::PS, G::T), grd(((2 * a.nx + G::PS - 1) / G::PS) * (2 * a.ny), nslots);
+    k_z<L><<<grd, blk, G::smem_strided, st>>>(a);
+  }
+  static cudaError_t setup() {
+    cudaError_t e = cudaSuccess;
+    {
+      e = cudaFuncSetAttribute(k_fx<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ix<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
+    }
+    return e;
+  }
+  static PassLaunch table() {
+    PassLaunch t;
+    t.fx = &fx; t.fy = &fy; t.iy = &iy; t.z = &z; t.ix = &ix;
+    t.rows_per_cta_contig = G::PC;
+    t.pencils_per_cta_strided = G::PS;
+    return t;
+  }
+};
+
+// Defined in one translation unit per length (passes_L*.cu).
+#define LS_DECLARE_LENGTH(L) \
+  PassLaunch pass_table_##L(); \
+  cudaError_t pass_setup_##L();
+LS_DECLARE_LENGTH(16)
+LS_DECLARE_LENGTH(24)
+LS_DECLARE_LENGTH(32)
+LS_DECLARE_LENGTH(48)
+LS_DECLARE_LENGTH(64)
+LS_DECLARE_LENGTH(96)
+LS_DECLARE_LENGTH(128)
+LS_DECLARE_LENGTH(192)
+LS_DECLARE_LENGTH(256)
+LS_DECLARE_LENGTH(384)
+#undef LS_DECLARE_LENGTH
+
+#define LS_DEFINE_LENGTH(L) \
+  PassLaunch pass_table_##L() { return PassImpl<L>::table(); } \
+  cudaError_t pass_setup_##L() { return PassImpl<L>::setup(); }
+
+}  // namespace lsgpu
