@@ -174,8 +174,10 @@ def oracle_sample(w, seconds_budget=12.0, iters_per_solve=None):
 def run_gpu(args):
     import torch
 
+    import __graft_entry__
+
+    __graft_entry__.build()
     import paper_1910_13844_gb300 as ls
-    from paper_1910_13844_gb300 import build as lsbuild
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -184,7 +186,6 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    lsbuild.build()
     w = WORKLOADS[args.workload]
     shape, Q = w["shape"], w["views"]
     kb = 2 * np.pi * ph.ETA_B / ph.LAMBDA_UM

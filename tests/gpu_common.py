@@ -13,9 +13,9 @@ def torch_and_lib():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_1910_13844_gb300 import build
+    import __graft_entry__
 
-    build.build()
+    __graft_entry__.build()
     import paper_1910_13844_gb300 as ls
 
     return torch, ls

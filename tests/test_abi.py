@@ -15,9 +15,9 @@ def _declared(repo_root):
 
 @pytest.fixture(scope="module")
 def lib(repo_root):
-    from paper_1910_13844_gb300 import build
+    import __graft_entry__
 
-    path = build.build()
+    path = __graft_entry__._build_module().build()
     return ctypes.CDLL(path)
 
 
