@@ -279,24 +279,30 @@ def run_gpu(args):
     value = ws * solves_per_step / (ms_step / 1e3)
     e2e_value = ws * solves_per_step / (ms_e2e_step / 1e3)
 
-    # roofline of the dominant kernel (the z pass: FFT, Green multiply, IFFT)
+    # roofline of the dominant kernel (the z pass: FFT, Green multiply, IFFT); bytes counted for the
+    # slots that actually ran (converged views are masked off inside the launches)
     N = shape[0] * shape[1] * shape[2]
     nz, ny, nx = shape
-    z_ms, z_launches, z_slots = prof["z"]
-    slots_per_launch = z_slots / max(z_launches, 1)
-    bytes_per_slot = 2 * 8 * (4 * N)                       # read + write of the nz x 2ny x 2nx pencils
     octant = 8 * (nx + 1) * (ny + 1) * (nz + 1)            # Green spectrum octant, read once per launch
-    bytes_per_launch = bytes_per_slot * slots_per_launch + octant
+    pass_bytes = {"fx": 28 * N, "fy": 48 * N, "z": 64 * N, "iy": 48 * N, "ix": 32 * N}   # plain-matvec model
+    pass_gbs = {}
+    mv_bytes = mv_ms = 0.0
+    for k, b in pass_bytes.items():
+        ms_k, launches_k, _, active_k = prof[k]
+        byt = b * active_k + (octant * launches_k if k == "z" else 0)
+        if ms_k > 0:
+            pass_gbs[k] = round(byt / (ms_k / 1e3) / 1e9, 1)
+        mv_bytes += byt
+        mv_ms += ms_k
+    z_ms, z_launches, _, z_active = prof["z"]
+    active_per_launch = z_active / max(z_launches, 1)
+    bytes_per_launch = 64 * N * active_per_launch + octant
     z_ms_launch = z_ms / max(z_launches, 1)
     achieved = bytes_per_launch / (z_ms_launch / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     tr = traffic_per_slot("z_pass")
     dominant = max((k for k in prof if k != "other"), key=lambda k: prof[k][0])
     total_kernel_ms = sum(v[0] for v in prof.values())
-    # whole-matvec GB/s: the five passes of one operator application
-    mv_ms = sum(prof[k][0] for k in ("fx", "fy", "z", "iy", "ix"))
-    mv_slot_passes = prof["z"][2]
-    mv_bytes = 228 * N * mv_slot_passes  # algorithmic bytes of one matvec pass structure (octant Ghat)
     launches = int(sum(v[1] for v in prof.values()))
 
     out = {
@@ -326,15 +332,17 @@ def run_gpu(args):
             "kernel": "k_z (z-pencil FFT, Green multiply, inverse FFT, crop)",
             "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-            "traffic": (round(tr * slots_per_launch) if tr is not None else None),
+            "traffic": (round(tr * active_per_launch) if tr is not None else None),
             "algorithmic_bytes_per_launch": int(bytes_per_launch),
-            "launch_ms": round(z_ms_launch, 4), "slots_per_launch": slots_per_launch,
+            "launch_ms": round(z_ms_launch, 4), "active_views_per_launch": round(active_per_launch, 2),
         },
         "matvec": {
             "gbs": round(mv_bytes / (mv_ms / 1e3) / 1e9, 1) if mv_ms else None,
             "frac_hbm": round(mv_bytes / (mv_ms / 1e3) / 1e9 / peak, 4) if mv_ms else None,
-            "us_per_view": round(1e3 * mv_ms / max(mv_slot_passes, 1), 2),
-            "bytes_model": "228 N bytes per view (F-x 28N, F-y 48N, Z 72N, I-y 48N, I-x 32N)",
+            "us_per_view": round(1e3 * mv_ms / max(prof["z"][3], 1), 2),
+            "pass_gbs": pass_gbs,
+            "bytes_model": "plain matvec per view: F-x 28N, F-y 48N, Z 64N + Ghat octant per launch, I-y 48N, "
+                           "I-x 32N bytes (the fused BiCGStab prologue/epilogue traffic is not counted)",
         },
         "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in prof.items()} if total_kernel_ms else {},
         "dominant_kernel": dominant,
@@ -391,7 +399,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="bench", choices=sorted(WORKLOADS))

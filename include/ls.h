@@ -220,6 +220,7 @@ typedef struct {
   double ms[LS_K_COUNT];          /* summed device time per kind (CUDA events around each launch) */
   long long launches[LS_K_COUNT]; /* launches per kind                                            */
   long long slot_passes[LS_K_COUNT]; /* sum over launches of the slots each launch covered        */
+  long long active_slot_passes[LS_K_COUNT]; /* slots that actually ran (not masked off), summed     */
 } ls_kernel_times;
 
 /* enable = 1: reset the counters and time every kernel launch of this plan

@@ -192,10 +192,13 @@ def ls_gradient(plan: int, f, residuals, grad, u_in=None, u_fwd=None, view_weigh
 
 
 def ls_profile(plan: int, enable: bool):
-    """Turn per-launch event timing on/off; returns {kind: (ms, launches, slot_passes)} so far."""
+    """Turn per-launch event timing on/off.
+
+    Returns {kind: (ms, launches, slot_passes, active_slot_passes)} accumulated so far."""
     t = _abi.ls_kernel_times()
     _check(_lib.ls_profile(plan, int(bool(enable)), C.byref(t)), "ls_profile")
-    return {name: (t.ms[i], t.launches[i], t.slot_passes[i]) for i, name in enumerate(_abi.LS_K_NAMES)}
+    return {name: (t.ms[i], t.launches[i], t.slot_passes[i], t.active_slot_passes[i])
+            for i, name in enumerate(_abi.LS_K_NAMES)}
 
 
 def ls_server_create(opt: ls_server_options) -> int:

@@ -56,7 +56,8 @@ LS_K_NAMES = ["fx", "fy", "z", "iy", "ix", "update", "scalar", "far", "other"]
 
 
 class ls_kernel_times(C.Structure):
-    _fields_ = [("ms", C.c_double * 9), ("launches", C.c_longlong * 9), ("slot_passes", C.c_longlong * 9)]
+    _fields_ = [("ms", C.c_double * 9), ("launches", C.c_longlong * 9), ("slot_passes", C.c_longlong * 9),
+                ("active_slot_passes", C.c_longlong * 9)]
 
 
 class ls_result(C.Structure):

@@ -164,6 +164,7 @@ static SlotSel sel_slots(ls_plan* P, unsigned mask) {
   s.mask = mask;
   s.f_default = nullptr;
   s.adj_default = 0;
+  s.runs = nullptr;
   return s;
 }
 
@@ -197,23 +198,30 @@ static StridedParams fy_base(ls_plan* P, SlotSel sel, const float2* src, size_t 
   return a;
 }
 
-static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx, IxParams ix, cudaStream_t st) {
+static SlotSel counted(ls_plan* P, SlotSel s, int kind) {
+  s.runs = P->prof.runs_d ? P->prof.runs_d + kind : nullptr;
+  return s;
+}
+
+static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_in, IxParams ix, cudaStream_t st) {
   Engine& e = P->eng;
+  FxParams fx = fx_in;
+  fx.sel = counted(P, fx.sel, LS_K_FX);
   timed(P, LS_K_FX, nslots, st, [&] { P->px.fx(fx, nslots, st); });
-  StridedParams fy = fy_base(P, sel, e.a1, e.a1_stride, e.a2, e.a2_stride, P->nz);
+  StridedParams fy = fy_base(P, counted(P, sel, LS_K_FY), e.a1, e.a1_stride, e.a2, e.a2_stride, P->nz);
   timed(P, LS_K_FY, nslots, st, [&] { P->py.fy(fy, nslots, st); });
   ZParams z;
-  z.sel = sel;
+  z.sel = counted(P, sel, LS_K_Z);
   z.nx = P->nx; z.ny = P->ny; z.nz = P->nz;
   z.a2 = e.a2; z.a2_stride = e.a2_stride;
   z.gocta = P->gocta;
   z.tw = P->tw_z;
   timed(P, LS_K_Z, nslots, st, [&] { P->pz.z(z, nslots, st); });
-  StridedParams iy = fy_base(P, sel, e.a2, e.a2_stride, e.a1, e.a1_stride, P->nz);
+  StridedParams iy = fy_base(P, counted(P, sel, LS_K_IY), e.a2, e.a2_stride, e.a1, e.a1_stride, P->nz);
   iy.src_plane = (size_t)2 * P->ny * 2 * P->nx;
   iy.dst_plane = (size_t)P->ny * 2 * P->nx;
   timed(P, LS_K_IY, nslots, st, [&] { P->py.iy(iy, nslots, st); });
-  ix.sel = sel;
+  ix.sel = counted(P, sel, LS_K_IX);
   ix.nx = P->nx;
   ix.rows = P->ny * P->nz;
   ix.src = e.a1; ix.src_stride = e.a1_stride;
@@ -297,7 +305,7 @@ void seq_iter(ls_plan* P, int nslots, cudaStream_t st) {
   // x += alpha p + omega s ; r = s - omega t
   {
     UpdParams u;
-    u.sel = sel;
+    u.sel = counted(P, sel, LS_K_UPDATE);
     u.n = e.N;
     u.vstride = e.N;
     u.x = e.vptr(V_X); u.r = e.vptr(V_R);
@@ -538,15 +546,24 @@ const char* ls_last_error(void) { return g_last_error; }
 int ls_profile(ls_plan* P, int enable, ls_kernel_times* out) {
   if (!P) { set_last_error("null plan"); return LS_EINVAL; }
   prof_resolve(P, true);
+  if (!P->prof.runs_d) {
+    LS_CUDA_TRY(cudaMalloc(&P->prof.runs_d, LS_K_COUNT * sizeof(unsigned long long)));
+    LS_CUDA_TRY(cudaMemset(P->prof.runs_d, 0, LS_K_COUNT * sizeof(unsigned long long)));
+  }
+  unsigned long long runs[LS_K_COUNT];
+  LS_CUDA_TRY(cudaDeviceSynchronize());
+  LS_CUDA_TRY(cudaMemcpy(runs, P->prof.runs_d, sizeof(runs), cudaMemcpyDeviceToHost));
   if (out) {
     for (int k = 0; k < LS_K_COUNT; ++k) {
       out->ms[k] = P->prof.ms[k];
       out->launches[k] = P->prof.launches[k];
       out->slot_passes[k] = P->prof.slot_passes[k];
+      out->active_slot_passes[k] = (long long)runs[k];
     }
   }
   if (enable) {
     for (int k = 0; k < LS_K_COUNT; ++k) P->prof.ms[k] = 0, P->prof.launches[k] = 0, P->prof.slot_passes[k] = 0;
+    LS_CUDA_TRY(cudaMemset(P->prof.runs_d, 0, LS_K_COUNT * sizeof(unsigned long long)));
   }
   P->prof.on = enable != 0;
   return LS_OK;
@@ -639,6 +656,7 @@ void ls_plan_destroy(ls_plan* P) {
   if (!P) return;
   prof_resolve(P, true);
   for (cudaEvent_t ev : P->prof.pool) cudaEventDestroy(ev);
+  cudaFree(P->prof.runs_d);
   engine_release(P->eng);
   cudaFree(P->tw_x); cudaFree(P->tw2_x); cudaFree(P->tw_y); cudaFree(P->tw_z);
   cudaFree(P->gocta); cudaFree(P->k2hat);
@@ -710,6 +728,7 @@ static int single_op(ls_plan* P, const float* f, const ls_c64* x, ls_c64* y, int
   if (rc) return rc;
   SlotSel sel;
   sel.slots = nullptr; sel.mask = 0; sel.f_default = f; sel.adj_default = adjoint ? 1 : 0;
+  sel.runs = nullptr;
   FxParams fx = fx_base(P, sel, P->ny * P->nz);
   fx.mode = matvec ? FX_F_TIMES : FX_COPY;
   fx.src = (const float2*)x;

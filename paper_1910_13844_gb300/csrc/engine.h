@@ -44,6 +44,7 @@ struct Profiler {
   struct Pending { int kind; int slots; cudaEvent_t a, b; };
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
+  unsigned long long* runs_d = nullptr;   // [LS_K_COUNT] slots that ran, counted by the kernels
   double ms[LS_K_COUNT] = {};
   long long launches[LS_K_COUNT] = {};
   long long slot_passes[LS_K_COUNT] = {};

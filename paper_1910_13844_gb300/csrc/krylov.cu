@@ -23,6 +23,7 @@ namespace lsgpu {
 __global__ void __launch_bounds__(256) k_update(UpdParams a) {
   const int slot = blockIdx.y;
   if (!slot_runs(a.sel, slot)) return;
+  count_run(a.sel);
   const SlotDev& sd = a.sel.slots[slot];
   const float2 al = make_float2((float)sd.alpha.x, (float)sd.alpha.y);
   const float2 om = make_float2((float)sd.omega.x, (float)sd.omega.y);

@@ -33,6 +33,7 @@ struct SlotSel {
   unsigned mask;          // run slot s iff (slots[s].flags & mask) != 0 (mask 0: all)
   const float* f_default; // potential when slots == null
   int adj_default;        // adjoint flag when slots == null
+  unsigned long long* runs;  // if set: +1 per slot that ran (counted by its first CTA)
 };
 
 struct FxParams {
@@ -85,6 +86,9 @@ struct IxParams {
 
 __device__ __forceinline__ bool slot_runs(const SlotSel& s, int slot) {
   return !(s.slots && s.mask && !(s.slots[slot].flags & s.mask));
+}
+__device__ __forceinline__ void count_run(const SlotSel& s) {
+  if (s.runs && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(s.runs, 1ull);
 }
 __device__ __forceinline__ const float* slot_f(const SlotSel& s, int slot) {
   return s.slots ? s.slots[slot].f : s.f_default;
@@ -156,6 +160,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC) k_fx(FxParams a) {
   extern __shared__ float2 sm[];
   const int slot = blockIdx.y;
   if (!slot_runs(a.sel, slot)) return;
+  count_run(a.sel);
   const int t = threadIdx.x, p = threadIdx.y;
   const int nx = L / 2;
   const int row = blockIdx.x * G::PC + p;
@@ -232,6 +237,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_strided(StridedParam
   extern __shared__ float2 sm[];
   const int slot = blockIdx.y;
   if (!slot_runs(a.sel, slot)) return;
+  count_run(a.sel);
   const int p = threadIdx.x, t = threadIdx.y;
   const int tiles_c = (a.ncont + P - 1) / P;
   const int plane = blockIdx.x / tiles_c;
@@ -287,6 +293,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_z(ZParams a) {
   extern __shared__ float2 sm[];
   const int slot = blockIdx.y;
   if (!slot_runs(a.sel, slot)) return;
+  count_run(a.sel);
   const int p = threadIdx.x, t = threadIdx.y;
   const int ncont = 2 * a.nx;
   const int tiles_c = (ncont + P - 1) / P;
@@ -359,6 +366,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC) k_ix(IxParams a) {
   extern __shared__ float2 sm[];
   const int slot = blockIdx.y;
   if (!slot_runs(a.sel, slot)) return;
+  count_run(a.sel);
   const int t = threadIdx.x, p = threadIdx.y;
   const int nx = L / 2;
   const int row = blockIdx.x * G::PC + p;
