@@ -36,6 +36,8 @@ METRIC = "LS matvec GB/s (%HBM) & solves/s at 128³×60 views; p50/p99 served so
 WORKLOADS = {
     "bench": dict(shape=(128, 128, 128), views=60, count=20, rmin=4.0, rmax=20.0, dn_max=0.05),
     "small": dict(shape=(32, 32, 32), views=4, count=4, rmin=2.0, rmax=6.0, dn_max=0.05),
+    # same grid and phantom as "bench" with 4 views: the case the full ncu captures run on
+    "profile": dict(shape=(128, 128, 128), views=4, count=20, rmin=4.0, rmax=20.0, dn_max=0.05),
 }
 TOL = 1e-6
 NA = 0.8
