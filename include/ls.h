@@ -129,6 +129,23 @@ int ls_apply_green(ls_plan* plan, const ls_c64* v, ls_c64* out, int adjoint, voi
 int ls_matvec(ls_plan* plan, const float* f, const ls_c64* x, ls_c64* y, int adjoint,
               void* cuda_stream);
 
+/* Same operator as ls_matvec (y = x - G (f .* x), or with G^H), for callers
+ * that cannot allocate device memory: a process whose device memory is all
+ * owned by its own pool, or a loop that must not stall on the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  ls_matvec may allocate the plan's
+ * workspace on first use; this call allocates nothing.  Its FFT
+ * intermediates live in one static device array of 64 MiB inside the library
+ * (48 bytes per voxel: grids up to 1398101 voxels, e.g. 96^3 or 128x128x64);
+ * every GPU that loads the library holds that array until the process exits.
+ * Larger grids return LS_EINVAL with the sizes in ls_last_error().  The first
+ * call on each device looks up the array's device address, so make that first
+ * call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (different streams, or different host threads) race and
+ * must be ordered by the caller.  Nothing has to be cleared between calls.
+ * The paper has no counterpart to this entry point. */
+int ls_matvec_noalloc(const ls_plan* plan, const float* f, const ls_c64* x, ls_c64* y, int adjoint,
+                      void* cuda_stream);
+
 /* Forward model for n_views illuminations of one potential f (eqs. lipp1, lipp2):
  * BiCGStab on (I - G diag f) u = u_in[q] from u = u_in[q], all views batched,
  * then the far field y_q = G~ (f .* u_q) on the detector.  u_out[q] (N) and
