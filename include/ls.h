@@ -129,6 +129,13 @@ int ls_apply_green(ls_plan* plan, const ls_c64* v, ls_c64* out, int adjoint, voi
 int ls_matvec(ls_plan* plan, const float* f, const ls_c64* x, ls_c64* y, int adjoint,
               void* cuda_stream);
 
+/* y[q] = x[q] - G (f .* x[q]) (adjoint != 0: with G^H) for n_views vectors at
+ * once: every FFT pass is one launch over all vectors (the batched form the
+ * solver uses).  x, y: host arrays of n_views device pointers (N complex64
+ * each; y[q] may equal x[q]). */
+int ls_matvec_batch(ls_plan* plan, const float* f, int n_views, const ls_c64* const* x, ls_c64* const* y,
+                    int adjoint, void* cuda_stream);
+
 /* Same operator as ls_matvec (y = x - G (f .* x), or with G^H), for callers
  * that cannot allocate device memory: a process whose device memory is all
  * owned by its own pool, or a loop that must not stall on the implicit device

@@ -27,7 +27,7 @@ __all__ = [
     "ls_scattering_potential", "ls_plane_waves", "ls_apply_green", "ls_matvec", "ls_forward", "ls_farfield",
     "ls_farfield_adjoint", "ls_residual", "ls_gradient", "ls_server_create", "ls_submit", "ls_poll",
     "ls_server_destroy", "ls_status_string", "ls_last_error", "ls_workspace_bytes", "ls_profile", "library_path",
-    "ls_matvec_noalloc",
+    "ls_matvec_noalloc", "ls_matvec_batch",
 ]
 
 _SOFT = (LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN, LS_TIMEOUT, LS_PENDING)
@@ -143,6 +143,16 @@ def ls_apply_green(plan: int, v, out, adjoint: bool = False, stream=None) -> int
 
 def ls_matvec(plan: int, f, x, y, adjoint: bool = False, stream=None) -> int:
     return _check(_lib.ls_matvec(plan, _ptr(f), _ptr(x), _ptr(y), int(bool(adjoint)), _stream(stream)), "ls_matvec")
+
+
+def ls_matvec_batch(plan: int, f, x, y, adjoint: bool = False, stream=None) -> int:
+    """y[q] = x[q] - G (f x[q]) for a list / [Q, ...] tensor of vectors, one batched launch per pass."""
+    ax, n = _views(x)
+    ay, m = _views(y)
+    if n != m:
+        raise ValueError("x and y need the same number of views")
+    return _check(_lib.ls_matvec_batch(plan, _ptr(f), n, ax, ay, int(bool(adjoint)), _stream(stream)),
+                  "ls_matvec_batch")
 
 
 def ls_matvec_noalloc(plan: int, f, x, y, adjoint: bool = False, stream=None) -> int:

@@ -92,6 +92,7 @@ SIGNATURES = {
     "ls_workspace_bytes": (C.c_size_t, [C.POINTER(ls_grid), C.c_int]),
     "ls_profile": (C.c_int, [_P, C.c_int, C.POINTER(ls_kernel_times)]),
     "ls_matvec_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int, _P]),
+    "ls_matvec_batch": (C.c_int, [_P, _P, C.c_int, _PP, _PP, C.c_int, _P]),
 }
 
 _lib = None

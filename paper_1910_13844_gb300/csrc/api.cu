@@ -765,6 +765,40 @@ static int check_views(int n, const void* const* a, const char* what, bool allow
   return LS_OK;
 }
 
+int ls_matvec_batch(ls_plan* P, const float* f, int n_views, const ls_c64* const* x, ls_c64* const* y, int adjoint,
+                    void* stream) {
+  if (!P || !f || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
+  int rc = check_views(n_views, (const void* const*)x, "x", false);
+  if (!rc) rc = check_views(n_views, (const void* const*)y, "y", false);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = engine_reserve(P, n_views);
+  if (rc) return rc;
+  Engine& e = P->eng;
+  for (int q = 0; q < n_views; ++q) {
+    LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_X, q), x[q], e.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    slot_defaults(P, e.slots_h[q], f, adjoint ? 1 : 0);
+    e.slots_h[q].flags = SLOT_AUX;
+  }
+  LS_CUDA_TRY(cudaMemcpyAsync(e.slots_d, e.slots_h, (size_t)n_views * sizeof(SlotDev), cudaMemcpyHostToDevice, st));
+  SlotSel sel = sel_slots(P, SLOT_AUX);
+  FxParams fx = fx_base(P, sel, P->ny * P->nz);
+  fx.mode = FX_F_TIMES;
+  fx.src = e.vptr(V_X);
+  IxParams ix;
+  memset(&ix, 0, sizeof(ix));
+  ix.mode = IX_MATVEC;
+  ix.in0 = e.vptr(V_X);
+  ix.out0 = e.vptr(V_R);
+  ix.vstride = e.N;
+  matvec_core(P, sel, n_views, fx, ix, st);
+  for (int q = 0; q < n_views; ++q)
+    LS_CUDA_TRY(cudaMemcpyAsync(y[q], e.vptr(V_R, q), e.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+  LS_CUDA_TRY(cudaGetLastError());
+  prof_resolve(P, false);
+  return LS_OK;
+}
+
 // Copy the caller's right-hand sides into slots [0, n) (b and x0 = b) and set the slot states.
 static int load_rhs(ls_plan* P, const float* f, int n, const ls_c64* const* rhs, int adjoint, cudaStream_t st) {
   Engine& e = P->eng;

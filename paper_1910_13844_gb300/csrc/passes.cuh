@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC) k_fx(FxParams a) {
   }
   float2* S = sm + (size_t)p * R1 * G::SROW;
   if (t < R2) {
-    Dft<R1, -1>::run(v);
+    Dft<R1, -1, R1 / 2, R1>::run(v);
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], __ldg(a.tw2 + k1 * R2 + t));
 #pragma unroll
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_strided(StridedParam
     }
   }
   if (t < R2) {
-    Dft<R1, DIR>::run(v);
+    Dft<R1, DIR, (DIR < 0 ? R1 / 2 : R1), R1>::run(v);
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) {
       float2 w = __ldg(a.tw + k1 * t);
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_strided(StridedParam
     float2 u[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) u[n2] = sm[(t * R2 + n2) * P + p];
-    Dft<R2, DIR>::run(u);
+    Dft<R2, DIR, R2, (DIR < 0 ? R2 : R2 / 2)>::run(u);
     float2* dst = a.dst + (size_t)slot * a.dst_stride + (size_t)plane * a.dst_plane + c;
     if (DIR < 0) {
 #pragma unroll
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_z(ZParams a) {
     for (int n1 = 0; n1 < R1 / 2; ++n1) v[n1] = col[(size_t)(R2 * n1 + t) * zstride];
   }
   if (t < R2) {
-    Dft<R1, -1>::run(v);
+    Dft<R1, -1, R1 / 2, R1>::run(v);
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], __ldg(a.tw + k1 * t));
 #pragma unroll
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_z(ZParams a) {
     float2 w[R1];
 #pragma unroll
     for (int m2 = 0; m2 < R1; ++m2) w[m2] = sm[(t * R1 + m2) * P + p];
-    Dft<R1, +1>::run(w);
+    Dft<R1, +1, R1, R1 / 2>::run(w);
     // outputs z = t + R2 j2, keep z < nz  (j2 < R1/2)
 #pragma unroll
     for (int j2 = 0; j2 < R1 / 2; ++j2) col[(size_t)(t + R2 * j2) * zstride] = w[j2];
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC) k_ix(IxParams a) {
     float2 u[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) u[n2] = S[t * G::SROW + n2];
-    Dft<R2, +1>::run(u);
+    Dft<R2, +1, R2, R2 / 2>::run(u);
     const size_t voff = (size_t)slot * a.vstride + (size_t)row * nx;
 #pragma unroll
     for (int k2 = 0; k2 < R2 / 2; ++k2) {

@@ -77,3 +77,20 @@ def test_operator_is_deterministic_and_linear():
     rhs = np.vdot(gha.cpu().numpy(), a.cpu().numpy())
     assert abs(lhs - rhs) < 1e-5 * abs(lhs)
     plan.close()
+
+
+@pytest.mark.gpu
+def test_batched_matvec_equals_single_matvecs():
+    torch, ls = torch_and_lib()
+    shape = (12, 16, 24)
+    plan = ls.Plan(shape, KB, H)
+    f = to_dev(torch, potential(ph.random_ellipsoids(shape, count=3, rmin=2, rmax=4)), torch.float32)
+    x = torch.stack([to_dev(torch, ph.random_field(shape, 60 + q), torch.complex64) for q in range(5)])
+    y = torch.empty_like(x)
+    ls.ls_matvec_batch(plan.handle, f, x, y, True)
+    for q in range(5):
+        yq = torch.empty_like(x[q])
+        ls.ls_matvec(plan.handle, f, x[q], yq, True)
+        torch.cuda.synchronize()
+        assert torch.equal(yq, y[q])
+    plan.close()
