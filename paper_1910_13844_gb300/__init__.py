@@ -27,7 +27,7 @@ __all__ = [
     "ls_scattering_potential", "ls_plane_waves", "ls_apply_green", "ls_matvec", "ls_forward", "ls_farfield",
     "ls_farfield_adjoint", "ls_residual", "ls_gradient", "ls_server_create", "ls_submit", "ls_poll",
     "ls_server_destroy", "ls_status_string", "ls_last_error", "ls_workspace_bytes", "ls_profile", "library_path",
-    "ls_matvec_noalloc", "ls_matvec_batch",
+    "ls_matvec_noalloc", "ls_matvec_batch", "Server",
 ]
 
 _SOFT = (LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN, LS_TIMEOUT, LS_PENDING)
@@ -294,3 +294,68 @@ class Plan:
         code, stats = ls_gradient(self.handle, f, residuals, g, u_in=u_in, u_fwd=u_fwd, view_weights=weights,
                                   stream=stream)
         return g, code, stats
+
+
+class Server:
+    """Owning wrapper of an ls_server (continuous batching of forward and gradient requests).
+
+    Tensors passed to ``submit_*`` must stay alive until ``poll`` reports the
+    request finished; this wrapper keeps references to them until then.
+    """
+
+    def __init__(self, k_b: float, voxel: float, tol: float = 1e-6, max_iter: int = 1000,
+                 hbm_budget_bytes: int = 0, max_views_per_grid: int = 0):
+        opt = ls_server_options(hbm_budget_bytes=hbm_budget_bytes, max_views_per_grid=max_views_per_grid,
+                                tol=tol, max_iter=max_iter, k_b=k_b, voxel=voxel)
+        self.handle = ls_server_create(opt)
+        self._keep = {}
+
+    def _submit(self, kind, f, kvec, meas=None, u_out=None, far=None, grad=None):
+        nz, ny, nx = f.shape
+        k = np.ascontiguousarray(np.asarray(kvec, dtype=np.float64).reshape(-1, 3))
+        loss = C.c_double(float("nan"))
+        req = ls_request(kind=kind, grid=ls_grid(nx, ny, nz), n_views=k.shape[0], f=_ptr(f),
+                         kvec=k.ctypes.data_as(C.POINTER(C.c_double)), meas=_ptr(meas), u_out=_ptr(u_out),
+                         far=_ptr(far), grad=_ptr(grad), loss=C.pointer(loss))
+        code, ticket = ls_submit(self.handle, req)
+        if code != LS_OK:
+            raise LsError(code, "ls_submit")
+        self._keep[ticket] = (f, k, meas, u_out, far, grad, loss)
+        return ticket
+
+    def submit_forward(self, f, kvec, u_out=None, far=None) -> int:
+        return self._submit(LS_REQ_FORWARD, f, kvec, u_out=u_out, far=far)
+
+    def submit_gradient(self, f, kvec, meas, grad, u_out=None) -> int:
+        return self._submit(LS_REQ_GRADIENT, f, kvec, meas=meas, grad=grad, u_out=u_out)
+
+    def poll(self, ticket: int):
+        """(status, info) with status LS_PENDING while running; info has 'ms', 'iterations_max', 'loss'."""
+        code, info = ls_poll(self.handle, ticket)
+        if code != LS_PENDING:
+            keep = self._keep.pop(ticket, None)
+            info["loss"] = keep[6].value if keep is not None else float("nan")
+        return code, info
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        import time as _t
+        t0 = _t.time()
+        while True:
+            code, info = self.poll(ticket)
+            if code != LS_PENDING:
+                return code, info
+            if _t.time() - t0 > timeout_s:
+                raise TimeoutError(f"request {ticket} still pending after {timeout_s} s")
+            _t.sleep(0.0005)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ls_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -57,6 +57,30 @@ static void radix_of(int L, int* R1, int* R2) {
   }
 }
 
+// Per-thread twiddle rows of the z pass: twa[t*R1 + k1] (t < R2) and twb[t*R2 + j1] (t < R1),
+// both exp(-2 pi i t k / L).
+static int make_z_twiddles(int L, float2** twa, float2** twb) {
+  int R1, R2;
+  radix_of(L, &R1, &R2);
+  const double pi = 3.14159265358979323846;
+  std::vector<float2> a(L), b(L);
+  for (int t = 0; t < R2; ++t)
+    for (int k = 0; k < R1; ++k) {
+      const int j = (t * k) % L;
+      a[t * R1 + k] = make_float2((float)cos(-2.0 * pi * j / L), (float)sin(-2.0 * pi * j / L));
+    }
+  for (int t = 0; t < R1; ++t)
+    for (int k = 0; k < R2; ++k) {
+      const int j = (t * k) % L;
+      b[t * R2 + k] = make_float2((float)cos(-2.0 * pi * j / L), (float)sin(-2.0 * pi * j / L));
+    }
+  LS_CUDA_TRY(cudaMalloc(twa, L * sizeof(float2)));
+  LS_CUDA_TRY(cudaMemcpy(*twa, a.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
+  LS_CUDA_TRY(cudaMalloc(twb, L * sizeof(float2)));
+  LS_CUDA_TRY(cudaMemcpy(*twb, b.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
+  return LS_OK;
+}
+
 // Twiddles computed in double on the host, rounded once to float.
 static int make_twiddles(int L, float2** tw, float2** tw2) {
   std::vector<float2> a(L), b(L);
@@ -216,6 +240,8 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   z.a2 = e.a2; z.a2_stride = e.a2_stride;
   z.gocta = P->gocta;
   z.tw = P->tw_z;
+  z.twa = P->twa_z;
+  z.twb = P->twb_z;
   timed(P, LS_K_Z, nslots, st, [&] { P->pz.z(z, nslots, st); });
   StridedParams iy = fy_base(P, counted(P, sel, LS_K_IY), e.a2, e.a2_stride, e.a1, e.a1_stride, P->nz);
   iy.src_plane = (size_t)2 * P->ny * 2 * P->nx;
@@ -360,6 +386,7 @@ void seq_far_adjoint(ls_plan* P, int nslots, const float2* const* r_dev_table, u
   Engine& e = P->eng;
   SlotSel sel = sel_slots(P, mask);
   PadParams pd;
+  pd.sel = sel;
   pd.nx = P->nx; pd.ny = P->ny; pd.mx = P->mx; pd.my = P->my; pd.ox = P->ox; pd.oy = P->oy;
   pd.src = r_dev_table;
   pd.dst = e.vptr(V_V);
@@ -399,7 +426,7 @@ void seq_far_adjoint(ls_plan* P, int nslots, const float2* const* r_dev_table, u
   timed(P, LS_K_IX, nslots, st, [&] { P->px.ix(ix, nslots, st); });
 }
 
-static int ensure_iter_graph(ls_plan* P, int nslots) {
+int ensure_iter_graph(ls_plan* P, int nslots) {
   Engine& e = P->eng;
   if (e.iter_graph && e.iter_graph_slots == nslots) return LS_OK;
   if (e.iter_graph) {
@@ -415,6 +442,33 @@ static int ensure_iter_graph(ls_plan* P, int nslots) {
   LS_CUDA_TRY(err);
   e.iter_graph_slots = nslots;
   return LS_OK;
+}
+
+ls_plan plan_slot_view(const ls_plan* P, int s0) {
+  ls_plan v;
+  v.nx = P->nx; v.ny = P->ny; v.nz = P->nz; v.N = P->N; v.kb = P->kb; v.h = P->h; v.opt = P->opt;
+  v.mx = P->mx; v.my = P->my; v.ox = P->ox; v.oy = P->oy; v.x_gamma = P->x_gamma;
+  v.px = P->px; v.py = P->py; v.pz = P->pz;
+  v.tw_x = P->tw_x; v.tw2_x = P->tw2_x; v.tw_y = P->tw_y; v.tw_z = P->tw_z;
+  v.twa_z = P->twa_z; v.twb_z = P->twb_z;
+  v.gocta = P->gocta; v.k2hat = P->k2hat; v.p_built = P->p_built;
+  const Engine& e = P->eng;
+  Engine& w = v.eng;
+  w = e;
+  w.vec = e.vec + (size_t)s0 * e.N;
+  w.a1 = e.a1 + (size_t)s0 * e.a1_stride;
+  w.a2 = e.a2 + (size_t)s0 * e.a2_stride;
+  w.far = e.far + (size_t)s0 * P->mx * P->my;
+  w.ucache = e.ucache ? e.ucache + (size_t)s0 * e.N : nullptr;
+  w.partials = e.partials + (size_t)s0 * e.maxparts * 4;
+  w.slots_d = e.slots_d + s0;
+  w.slots_h = e.slots_h + s0;
+  w.ptrs_d = e.ptrs_d + s0;
+  w.kvec_d = e.kvec_d + 3 * (size_t)s0;
+  w.weights_d = e.weights_d + s0;
+  w.iter_graph = nullptr;
+  w.cap_stream = nullptr;
+  return v;
 }
 
 int engine_solve(ls_plan* P, int nslots, cudaStream_t st) {
@@ -623,6 +677,7 @@ int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel, c
   rc = make_twiddles(L[0], &P->tw_x, &P->tw2_x);
   if (rc == LS_OK) rc = make_twiddles(L[1], &P->tw_y, nullptr);
   if (rc == LS_OK) rc = make_twiddles(L[2], &P->tw_z, nullptr);
+  if (rc == LS_OK) rc = make_z_twiddles(L[2], &P->twa_z, &P->twb_z);
   if (rc == LS_OK) {
     if (cudaMalloc(&P->gocta, (size_t)(P->nx + 1) * (P->ny + 1) * (P->nz + 1) * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&P->k2hat, (size_t)4 * P->N * sizeof(float2)) != cudaSuccess) {
@@ -659,6 +714,7 @@ void ls_plan_destroy(ls_plan* P) {
   cudaFree(P->prof.runs_d);
   engine_release(P->eng);
   cudaFree(P->tw_x); cudaFree(P->tw2_x); cudaFree(P->tw_y); cudaFree(P->tw_z);
+  cudaFree(P->twa_z); cudaFree(P->twb_z);
   cudaFree(P->gocta); cudaFree(P->k2hat);
   delete P;
 }

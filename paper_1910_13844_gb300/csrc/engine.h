@@ -61,6 +61,7 @@ struct ls_plan {
   double x_gamma = 0;
   lsgpu::PassLaunch px{}, py{}, pz{};
   float2 *tw_x = nullptr, *tw2_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
+  float2 *twa_z = nullptr, *twb_z = nullptr;
   float2* gocta = nullptr;
   float2* k2hat = nullptr;
   int p_built = 0;
@@ -85,6 +86,9 @@ void seq_far_adjoint(ls_plan* P, int nslots, const float2* const* r_dev_table, u
 int engine_upload_ptrs(ls_plan* P, int table, const void* const* host_ptrs, int n, cudaStream_t st);
 void** engine_ptr_table(ls_plan* P, int table);
 void slot_defaults(const ls_plan* P, SlotDev& s, const float* f, int adjoint);
+int ensure_iter_graph(ls_plan* P, int nslots);
+// Shallow view of slots [s0, s0 + n) of P's engine as slots [0, n) (no ownership).
+ls_plan plan_slot_view(const ls_plan* P, int s0);
 
 // Launch wrapper: when profiling is on, bracket the launch with an event pair.
 cudaEvent_t prof_event(ls_plan* P);

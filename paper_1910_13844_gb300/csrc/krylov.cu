@@ -244,6 +244,7 @@ __global__ void k_far_adjoint_mul(FarParams a) {
 // plane[s][y][x] = r[s][y - oy][x - ox] inside the detector window, 0 outside
 __global__ void k_pad_detector(PadParams a) {
   const int slot = blockIdx.y;
+  if (!slot_runs(a.sel, slot)) return;
   const size_t n = (size_t)a.ny * a.nx;
   const float2* r = a.src[slot];
   float2* dst = a.dst + (size_t)slot * a.dst_stride;

@@ -41,6 +41,7 @@ struct FarParams {
 };
 
 struct PadParams {
+  SlotSel sel;
   int nx, ny, mx, my, ox, oy;
   const float2* const* src;   // device array of per-slot detector arrays
   float2* dst; size_t dst_stride;

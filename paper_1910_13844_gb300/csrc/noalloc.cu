@@ -109,6 +109,8 @@ extern "C" int ls_matvec_noalloc(const ls_plan* P, const float* f, const ls_c64*
   z.a2 = a2; z.a2_stride = a2n;
   z.gocta = P->gocta;
   z.tw = P->tw_z;
+  z.twa = P->twa_z;
+  z.twb = P->twb_z;
   P->pz.z(z, 1, st);
 
   StridedParams iy = fy;

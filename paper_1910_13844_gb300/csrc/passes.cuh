@@ -67,6 +67,8 @@ struct ZParams {
   float2* a2; size_t a2_stride;
   const float2* gocta;         // [(nz+1)][(ny+1)][(nx+1)], scaled by 1/(8 nx ny nz)
   const float2* tw;
+  const float2* twa;           // twa[t*R1 + k1] = exp(-2 pi i t k1 / L), t < R2 (forward split)
+  const float2* twb;           // twb[t*R2 + j1] = exp(-2 pi i t j1 / L), t < R1 (transposed split)
 };
 
 struct IxParams {
@@ -117,6 +119,7 @@ struct Geo {
   static constexpr int T = imax(R1, R2);
   static constexpr int PC = (256 / T) > 0 ? (256 / T) : 1;   // rows per CTA, contiguous passes
   static constexpr int PS = 16;                              // pencils per CTA, strided passes
+  static constexpr int ZMINB = (T * PS > 256) ? 2 : ((T * PS == 256) ? 3 : 4);   // resident CTAs per SM asked of the z pass
   static constexpr int SROW = R2 + 1;                        // padded row of the contiguous exchange
   static constexpr size_t smem_contig = (size_t)PC * R1 * SROW * sizeof(float2);
   static constexpr size_t smem_strided = (size_t)L * PS * sizeof(float2);
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_strided(StridedParam
 
 // ------------------------------------------------------------------------- Z
 template <int L>
-__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_z(ZParams a) {
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS, Geo<L>::ZMINB) k_z(ZParams a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2, P = G::PS;
   extern __shared__ float2 sm[];
@@ -312,8 +315,14 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_z(ZParams a) {
   }
   if (t < R2) {
     Dft<R1, -1, R1 / 2, R1>::run(v);
+    // stage twiddles exp(-2 pi i t k1 / L), read two at a time from this thread's row
+    const float4* tw4 = reinterpret_cast<const float4*>(a.twa + t * R1);
 #pragma unroll
-    for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], __ldg(a.tw + k1 * t));
+    for (int k = 0; k < R1 / 2; ++k) {
+      const float4 w = __ldg(tw4 + k);
+      if (k > 0) v[2 * k] = cmul(v[2 * k], make_float2(w.x, w.y));
+      v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
+    }
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) sm[(k1 * R2 + t) * P + p] = v[k1];
   }
@@ -323,23 +332,30 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_z(ZParams a) {
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) u[n2] = sm[(t * R2 + n2) * P + p];
     Dft<R2, -1>::run(u);
-    // Green multiply: u[k2] holds kz = t + R1 k2; Ghat is even, read from one octant
+    // Green multiply: u[k2] holds kz = t + R1 k2; Ghat is even, read from one octant.
+    // Since nz = L/2, kz <= nz exactly when k2 < R2/2 (kz = nz only for t = 0, k2 = R2/2,
+    // where both folds agree), so the fold is known per k2 at compile time.
     const int fx = kx <= a.nx ? kx : ncont - kx;
     const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
-    const float2* g = a.gocta + (size_t)fy * (a.nx + 1) + (valid ? fx : 0);
     const size_t gz = (size_t)(a.ny + 1) * (a.nx + 1);
+    const float2* glo = a.gocta + (size_t)fy * (a.nx + 1) + (valid ? fx : 0) + (size_t)t * gz;   // kz = t + R1 k2
+    const float2* ghi = a.gocta + (size_t)fy * (a.nx + 1) + (valid ? fx : 0) + (size_t)(L - t) * gz;   // L - kz
+    const size_t gstep = (size_t)R1 * gz;
     const bool adj = slot_adj(a.sel, slot) != 0;
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) {
-      const int kz = t + R1 * k2;
-      const int fz = kz <= a.nz ? kz : 2 * a.nz - kz;
-      float2 gv = __ldg(g + (size_t)fz * gz);
+      const float2 gv = k2 < R2 / 2 ? __ldg(glo + k2 * gstep) : __ldg(ghi - k2 * gstep);
       u[k2] = adj ? cmulc(u[k2], gv) : cmul(u[k2], gv);
     }
     // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
     Dft<R2, +1>::run(u);
+    const float4* twb4 = reinterpret_cast<const float4*>(a.twb + t * R2);
 #pragma unroll
-    for (int j1 = 1; j1 < R2; ++j1) u[j1] = cmulc(u[j1], __ldg(a.tw + j1 * t));
+    for (int k = 0; k < R2 / 2; ++k) {
+      const float4 w = __ldg(twb4 + k);
+      if (k > 0) u[2 * k] = cmulc(u[2 * k], make_float2(w.x, w.y));
+      u[2 * k + 1] = cmulc(u[2 * k + 1], make_float2(w.z, w.w));
+    }
   }
   __syncthreads();
   if (t < R1) {
