@@ -1,0 +1,94 @@
+"""Parity at the full workload sizes, in the bench's launch configuration, on outputs the FP64 oracle can
+compute one by one: 128^3 x 60 views (batched forward) and 128 x 128 x 96 x 40 views (forward + gradient)."""
+import numpy as np
+import pytest
+
+import phantoms as ph
+from oracle import green, model
+
+from gpu_common import ETA_B, H, KB, LAM, rel, to_dev, torch_and_lib
+
+
+@pytest.mark.gpu
+def test_bench_workload_128cube_60_views():
+    torch, ls = torch_and_lib()
+    shape = (128, 128, 128)
+    dn = ph.random_ellipsoids(shape, count=20, rmin=4, rmax=20, dn_max=0.05)
+    f64 = green.scattering_potential(dn, ETA_B, LAM)
+    kvec = ph.cone_directions(60, 0.8) * KB
+    plan = ls.Plan(shape, KB, H, tol=1e-6)
+    f = to_dev(torch, f64, torch.float32)
+    uin = plan.plane_waves(kvec)
+    u, far, code, stats = plan.forward(f, uin)
+    torch.cuda.synchronize()
+    assert code == ls.LS_OK
+    assert all(s["true_rel_residual"] <= 1e-5 for s in stats)
+    st = model.setup_from_optics(shape, LAM, ETA_B, H)
+    op = model.Operator(st, kernel_method="prop1")
+    f32 = f.cpu().numpy().astype(np.float64)
+    # FP64 residual of the GPU fields for two views (any size: ||u_in - A u|| / ||u_in||)
+    for q in (0, 37):
+        ug = u[q].cpu().numpy().astype(np.complex128)
+        ui = model.plane_wave(shape, H, kvec[q])
+        assert np.linalg.norm(ui - op.A(ug, f32)) / np.linalg.norm(ui) < 2e-5
+    # one view solved by the oracle: total field and far field
+    q = 11
+    ui = model.plane_wave(shape, H, kvec[q])
+    uo = model.forward(op, f32, ui, tol=1e-10)
+    assert rel(u[q].cpu().numpy(), uo) < 1e-4
+    assert rel(far[q].cpu().numpy(), op.farfield_fft(f32 * uo)) < 1e-4
+    # far field of the GPU fields at sampled pixels by direct summation (eq. Gtild-1)
+    rng = np.random.default_rng(5)
+    pix = [(int(a), int(b)) for a, b in rng.integers(0, 128, size=(24, 2))]
+    for q in (3, 59):
+        v = f32 * u[q].cpu().numpy().astype(np.complex128)
+        direct = op.farfield_pixels(v, pix)
+        got = np.array([complex(far[q, a, b]) for a, b in pix])
+        assert np.max(np.abs(got - direct)) < 2e-5 * np.max(np.abs(far[q].cpu().numpy()))
+    plan.close()
+
+
+@pytest.mark.gpu
+def test_cell_workload_128x128x96_40_views_gradient():
+    torch, ls = torch_and_lib()
+    shape = (96, 128, 128)
+    f_true64 = green.scattering_potential(ph.cell(shape), ETA_B, LAM)
+    kvec = ph.cone_directions(40, 0.8) * KB
+    plan = ls.Plan(shape, KB, H, tol=1e-7)
+    f_true = to_dev(torch, f_true64, torch.float32)
+    uin = plan.plane_waves(kvec)
+    _, y0, code, _ = plan.forward(f_true, uin, want_fields=False)
+    assert code == ls.LS_OK
+    noise = torch.from_numpy(ph.complex_normal(tuple(y0.shape)).astype(np.complex64)).cuda()
+    yn = torch.linalg.vector_norm(y0.reshape(40, -1), dim=1)
+    y = y0 + 0.01 * (yn / np.sqrt(2 * y0[0].numel())).reshape(40, 1, 1) * noise
+    w = np.array([1.0 / float(torch.vdot(m.flatten(), m.flatten()).real) for m in y])
+    f0 = 0.9 * f_true
+    u, far, code, _ = plan.forward(f0, uin)
+    res = torch.empty_like(far)
+    l2 = ls.ls_residual(far, y, res)
+    g, code, stats = plan.gradient(f0, res, u_fwd=u, weights=w)
+    torch.cuda.synchronize()
+    assert code == ls.LS_OK
+    # per-view gradients of two views against the oracle (forward + adjoint in FP64)
+    st = model.setup_from_optics(shape, LAM, ETA_B, H)
+    op = model.Operator(st, kernel_method="prop1")
+    f032 = f0.cpu().numpy().astype(np.float64)
+    for q in (0, 23):
+        gq, _, _ = plan.gradient(f0, res[q:q + 1].contiguous(), u_fwd=u[q:q + 1].contiguous(), weights=[w[q]])
+        uo = model.forward(op, f032, model.plane_wave(shape, H, kvec[q]), tol=1e-10)
+        ro = op.farfield_fft(f032 * uo) - y[q].cpu().numpy().astype(np.complex128)
+        go = model.gradient(op, f032, [None], residuals=[ro], weights=[w[q]], us=[uo], tol=1e-10)
+        assert rel(gq.cpu().numpy(), go) < 1e-3
+    # central finite difference of the full 40-view loss along a seeded direction, step 1e-3 ||f||_inf
+    d = torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, shape) * (f_true64 > 0)).float().cuda()
+    eps = 1e-3 * float(f_true.abs().max())
+
+    def L(fp):
+        _, fr, _, _ = plan.forward(fp, uin, want_fields=False)
+        rr = torch.empty_like(fr)
+        return 0.5 * float(np.sum(ls.ls_residual(fr, y, rr) * w))
+
+    fd = (L(f0 + eps * d) - L(f0 - eps * d)) / (2 * eps)
+    assert float((g.double() * d.double()).sum()) == pytest.approx(fd, rel=2e-2)
+    plan.close()
