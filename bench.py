@@ -380,6 +380,11 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(grad.numel() * 4)},
     }
     out["clocks"] = clocks.summary()
+    if ws == 1 and args.serve_requests_in_step_line > 0 and args.workload == "bench":
+        plan.close()
+        plan = None
+        torch.cuda.empty_cache()
+        out["serving"] = run_serving(torch, ls, args.serve_requests_in_step_line, load=0.8)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         ips = float(np.mean(stats_acc["fwd_iters"] + stats_acc["adj_iters"]))
         cb = oracle_sample(w, iters_per_solve=ips)
@@ -391,9 +396,146 @@ def run_gpu(args):
                                          f"oracle kernel build excluded"}
     if rank == 0:
         print(json.dumps(out))
-    plan.close()
+    if plan is not None:
+        plan.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- serving (continuous batching)
+SERVE_GRIDS = [(64, 64, 64), (96, 96, 96), (128, 128, 128), (192, 192, 192)]
+
+
+def serve_requests(n, seed=2026):
+    """Seeded request mix: grid uniform over SERVE_GRIDS, 8-60 views, 70% forward / 30% gradient."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        shape = SERVE_GRIDS[int(rng.integers(len(SERVE_GRIDS)))]
+        out.append({"shape": shape, "views": int(rng.integers(8, 61)), "grad": bool(rng.random() < 0.3),
+                    "seed": int(rng.integers(1 << 30))})
+    return out
+
+
+def run_serving(torch, ls, n_requests, load=0.8, seed=2026, calib=12, baseline_requests=6):
+    """Poisson arrivals at `load` x the measured batched capacity; returns latency and throughput."""
+    import time as _t
+
+    kb = 2 * np.pi * ph.ETA_B / ph.LAMBDA_UM
+    dev = torch.device("cuda")
+    pot = {}
+
+    def potential_for(shape, s):
+        key = (shape, s % 4)
+        if key not in pot:
+            dn = ph.random_ellipsoids(shape, count=8, rmin=shape[0] / 32, rmax=shape[0] / 6, dn_max=0.05, seed=s % 4)
+            dnd = torch.from_numpy(dn.astype(np.float32)).to(dev)
+            f = torch.empty_like(dnd)
+            ls.ls_scattering_potential(dnd, ph.ETA_B, kb, f)
+            pot[key] = f
+        return pot[key]
+
+    def make(r):
+        f = potential_for(r["shape"], r["seed"])
+        k = ph.cone_directions(r["views"], NA, ph.ETA_B) * kb
+        Q, (nz, ny, nx) = r["views"], r["shape"]
+        far = torch.empty((Q, ny, nx), dtype=torch.complex64, device=dev)
+        out = {"f": f, "k": k, "far": far}
+        if r["grad"]:
+            out["meas"] = torch.from_numpy((ph.complex_normal((Q, ny, nx), seed=r["seed"]) * 1e-3)
+                                           .astype(np.complex64)).to(dev)
+            out["g"] = torch.empty(r["shape"], dtype=torch.float32, device=dev)
+        return out
+
+    def submit(srv, r, bufs):
+        if r["grad"]:
+            return srv.submit_gradient(bufs["f"], bufs["k"], bufs["meas"], bufs["g"])
+        return srv.submit_forward(bufs["f"], bufs["k"], far=bufs["far"])
+
+    reqs = serve_requests(n_requests + calib, seed)
+    srv = ls.Server(kb, ph.VOXEL_UM, tol=TOL)
+    # warm the lanes (plan build per grid) outside the measurement
+    for shape in SERVE_GRIDS:
+        w = {"shape": shape, "views": 8, "grad": False, "seed": 0}
+        srv.wait(submit(srv, w, make(w)))
+    # capacity: a burst of `calib` requests submitted at once
+    t0 = _t.perf_counter()
+    burst = [(r, make(r)) for r in reqs[:calib]]
+    tick = [submit(srv, r, b) for r, b in burst]
+    for t in tick:
+        srv.wait(t)
+    t_burst = _t.perf_counter() - t0
+    solves = lambda r: r["views"] * (2 if r["grad"] else 1)  # noqa: E731
+    cap_rps = calib / t_burst
+    rate = load * cap_rps
+    rng = np.random.default_rng(seed + 1)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    pending, lat, total_solves = {}, [], 0
+    bufs_keep = {}
+    t0 = _t.perf_counter()
+    i = 0
+    while i < n_requests or pending:
+        now = _t.perf_counter() - t0
+        while i < n_requests and arrivals[i] <= now:
+            r = reqs[calib + i]
+            b = make(r)
+            t = submit(srv, r, b)
+            pending[t] = r
+            bufs_keep[t] = b
+            i += 1
+        for t in list(pending):
+            code, info = srv.poll(t)
+            if code != ls.LS_PENDING:
+                lat.append(info["ms"])
+                total_solves += solves(pending.pop(t))
+                bufs_keep.pop(t, None)
+        _t.sleep(0.0005)
+    wall = _t.perf_counter() - t0
+    srv.close()
+    # one-view-at-a-time GPU solves of a few requests (same kernels, Q = 1 per call, no batching)
+    base_solves, t_base = 0, 0.0
+    plans = {}
+    for r in reqs[calib:calib + baseline_requests]:
+        b = make(r)
+        if r["shape"] not in plans:
+            plans[r["shape"]] = ls.Plan(r["shape"], kb, ph.VOXEL_UM, tol=TOL)
+        plan = plans[r["shape"]]
+        torch.cuda.synchronize()
+        ts = _t.perf_counter()
+        for q in range(r["views"]):
+            uin = plan.plane_waves(b["k"][q:q + 1])
+            u, far, code, _ = plan.forward(b["f"], uin)
+            if r["grad"]:
+                res = torch.empty_like(far)
+                ls.ls_residual(far, b["meas"][q:q + 1].contiguous(), res)
+                plan.gradient(b["f"], res, u_fwd=u)
+        torch.cuda.synchronize()
+        t_base += _t.perf_counter() - ts
+        base_solves += solves(r)
+    for p in plans.values():
+        p.close()
+    lat = np.array(lat)
+    return {
+        "requests": n_requests, "load": load, "rate_rps": round(rate, 3), "capacity_rps": round(cap_rps, 3),
+        "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
+        "mean_ms": round(float(lat.mean()), 2), "solves_per_s": round(total_solves / wall, 2),
+        "one_view_at_a_time_solves_per_s": round(base_solves / t_base, 2) if t_base else None,
+        "mix": "grids {64,96,128,192}^3, 8-60 views, 70% forward / 30% gradient, dn <= 0.05, seed 2026",
+    }
+
+
+def run_serve_mode(args):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1910_13844_gb300 as ls
+
+    out = {"mode": "serve", "metric": METRIC}
+    for load in args.loads:
+        out[f"load_{load}"] = run_serving(torch, ls, args.requests, load=load)
+    print(json.dumps(out))
 
 
 # ----------------------------------------------------------------------------- reference arm (the oracle)
@@ -432,7 +574,14 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="bench", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving benchmark (Poisson request stream) instead")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 1.0])
+    ap.add_argument("--serve-requests-in-step-line", type=int, default=60)
     args = ap.parse_args()
+    if args.serve:
+        run_serve_mode(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

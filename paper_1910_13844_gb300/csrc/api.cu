@@ -132,6 +132,10 @@ static int max_parts(const ls_plan* P) {
 
 int engine_reserve(ls_plan* P, int nslots) {
   Engine& e = P->eng;
+  if (nslots > kMaxLaunchSlots) {
+    set_last_error("at most %d views per call (got %d)", kMaxLaunchSlots, nslots);
+    return LS_EINVAL;
+  }
   if (nslots <= e.cap) return LS_OK;
   // keep the slot-independent pieces; reallocate the per-slot arrays
   Engine old = e;
@@ -189,6 +193,7 @@ static SlotSel sel_slots(ls_plan* P, unsigned mask) {
   s.f_default = nullptr;
   s.adj_default = 0;
   s.runs = nullptr;
+  s.nslots = 0;
   return s;
 }
 
@@ -785,6 +790,7 @@ static int single_op(ls_plan* P, const float* f, const ls_c64* x, ls_c64* y, int
   SlotSel sel;
   sel.slots = nullptr; sel.mask = 0; sel.f_default = f; sel.adj_default = adjoint ? 1 : 0;
   sel.runs = nullptr;
+  sel.nslots = 1;
   FxParams fx = fx_base(P, sel, P->ny * P->nz);
   fx.mode = matvec ? FX_F_TIMES : FX_COPY;
   fx.src = (const float2*)x;

@@ -77,6 +77,7 @@ extern "C" int ls_matvec_noalloc(const ls_plan* P, const float* f, const ls_c64*
   sel.f_default = f;
   sel.adj_default = adjoint ? 1 : 0;
   sel.runs = nullptr;
+  sel.nslots = 1;
 
   FxParams fx = {};
   fx.sel = sel;
