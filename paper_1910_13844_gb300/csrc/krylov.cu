@@ -21,50 +21,39 @@ namespace lsgpu {
 // ------------------------------------------------------------------ update
 // x += alpha p + omega s ; r = s - omega t ; partials <rh, r>, ||r||^2
 __global__ void __launch_bounds__(256) k_update(UpdParams a) {
-  __shared__ int s_list[kMaxLaunchSlots];
-  __shared__ int s_ws[32];
-  const int nact = build_active(a.sel, s_list, s_ws);
+  const int slot = blockIdx.y;
+  if (!slot_runs(a.sel, slot)) return;
+  count_run(a.sel);
+  const SlotDev& sd = a.sel.slots[slot];
+  const float2 al = make_float2((float)sd.alpha.x, (float)sd.alpha.y);
+  const float2 om = make_float2((float)sd.omega.x, (float)sd.omega.y);
+  const size_t base = (size_t)slot * a.vstride;
+  const float4* p = reinterpret_cast<const float4*>(a.p + base);
+  const float4* s = reinterpret_cast<const float4*>(a.s + base);
+  const float4* t = reinterpret_cast<const float4*>(a.t + base);
+  const float4* rh = reinterpret_cast<const float4*>(a.rh + base);
+  float4* x = reinterpret_cast<float4*>(a.x + base);
+  float4* r = reinterpret_cast<float4*>(a.r + base);
   const size_t n4 = a.n / 2;
-  const int chunks = a.chunks;
-  const size_t len = (n4 + chunks - 1) / chunks;
-#pragma unroll 1
-  for (int item = blockIdx.x; item < nact * chunks; item += gridDim.x) {
-    const int slot = s_list[item / chunks];
-    const int chunk = item % chunks;
-    count_run(a.sel, chunk);
-    const SlotDev& sd = a.sel.slots[slot];
-    const float2 al = make_float2((float)sd.alpha.x, (float)sd.alpha.y);
-    const float2 om = make_float2((float)sd.omega.x, (float)sd.omega.y);
-    const size_t base = (size_t)slot * a.vstride;
-    const float4* p = reinterpret_cast<const float4*>(a.p + base);
-    const float4* s = reinterpret_cast<const float4*>(a.s + base);
-    const float4* t = reinterpret_cast<const float4*>(a.t + base);
-    const float4* rh = reinterpret_cast<const float4*>(a.rh + base);
-    float4* x = reinterpret_cast<float4*>(a.x + base);
-    float4* r = reinterpret_cast<float4*>(a.r + base);
-    const size_t beg = (size_t)chunk * len;
-    const size_t end = beg + len < n4 ? beg + len : n4;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (size_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-      float4 pv = __ldg(p + i), sv = __ldg(s + i), tv = __ldg(t + i), hv = __ldg(rh + i), xv = x[i];
-      float2 p0 = make_float2(pv.x, pv.y), p1 = make_float2(pv.z, pv.w);
-      float2 s0 = make_float2(sv.x, sv.y), s1 = make_float2(sv.z, sv.w);
-      float2 t0 = make_float2(tv.x, tv.y), t1 = make_float2(tv.z, tv.w);
-      float2 x0 = cadd(make_float2(xv.x, xv.y), cadd(cmul(al, p0), cmul(om, s0)));
-      float2 x1 = cadd(make_float2(xv.z, xv.w), cadd(cmul(al, p1), cmul(om, s1)));
-      float2 r0 = csub(s0, cmul(om, t0));
-      float2 r1 = csub(s1, cmul(om, t1));
-      x[i] = make_float4(x0.x, x0.y, x1.x, x1.y);
-      r[i] = make_float4(r0.x, r0.y, r1.x, r1.y);
-      float2 d0 = cdotterm(make_float2(hv.x, hv.y), r0);
-      float2 d1 = cdotterm(make_float2(hv.z, hv.w), r1);
-      acc[0] += d0.x + d1.x;
-      acc[1] += d0.y + d1.y;
-      acc[2] += r0.x * r0.x + r0.y * r0.y + r1.x * r1.x + r1.y * r1.y;
-    }
-    block_sum_store<4>(acc, a.partials + ((size_t)slot * chunks + chunk) * 4);
-    __syncthreads();
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    float4 pv = __ldg(p + i), sv = __ldg(s + i), tv = __ldg(t + i), hv = __ldg(rh + i), xv = x[i];
+    float2 p0 = make_float2(pv.x, pv.y), p1 = make_float2(pv.z, pv.w);
+    float2 s0 = make_float2(sv.x, sv.y), s1 = make_float2(sv.z, sv.w);
+    float2 t0 = make_float2(tv.x, tv.y), t1 = make_float2(tv.z, tv.w);
+    float2 x0 = cadd(make_float2(xv.x, xv.y), cadd(cmul(al, p0), cmul(om, s0)));
+    float2 x1 = cadd(make_float2(xv.z, xv.w), cadd(cmul(al, p1), cmul(om, s1)));
+    float2 r0 = csub(s0, cmul(om, t0));
+    float2 r1 = csub(s1, cmul(om, t1));
+    x[i] = make_float4(x0.x, x0.y, x1.x, x1.y);
+    r[i] = make_float4(r0.x, r0.y, r1.x, r1.y);
+    float2 d0 = cdotterm(make_float2(hv.x, hv.y), r0);
+    float2 d1 = cdotterm(make_float2(hv.z, hv.w), r1);
+    acc[0] += d0.x + d1.x;
+    acc[1] += d0.y + d1.y;
+    acc[2] += r0.x * r0.x + r0.y * r0.y + r1.x * r1.x + r1.y * r1.y;
   }
+  block_sum_store<4>(acc, a.partials + ((size_t)slot * gridDim.x + blockIdx.x) * 4);
 }
 
 // ------------------------------------------------------------------ scalar steps
@@ -297,20 +286,8 @@ __global__ void __launch_bounds__(256) k_residual(ResidualParams a) {
 }
 
 // ------------------------------------------------------------------ launchers
-void launch_update(const UpdParams& a0, int nblocks, int nslots, cudaStream_t st) {
-  static int max_ctas = 0;
-  if (max_ctas == 0) {
-    int dev = 0, sms = 0, nb = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update, 256, 0);
-    max_ctas = (nb > 0 ? nb : 1) * (sms > 0 ? sms : 1);
-  }
-  UpdParams a = a0;
-  a.sel.nslots = nslots;
-  a.chunks = nblocks;
-  const long long items = (long long)nblocks * nslots;
-  k_update<<<(int)(items < max_ctas ? items : max_ctas), 256, 0, st>>>(a);
+void launch_update(const UpdParams& a, int nblocks, int nslots, cudaStream_t st) {
+  k_update<<<dim3(nblocks, nslots), 256, 0, st>>>(a);
 }
 void launch_scalar(const ScalarParams& a, int nslots, cudaStream_t st) {
   k_scalar<<<nslots, 256, 0, st>>>(a);

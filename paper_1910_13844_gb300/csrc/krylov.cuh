@@ -10,7 +10,6 @@ enum ScalarPhase : int { PH_RESID = 0, PH_ALPHA = 1, PH_OMEGA = 2, PH_RHO = 3 };
 
 struct UpdParams {
   SlotSel sel;
-  int chunks;                 // work items per slot (each sums its own partials)
   size_t n, vstride;
   float2 *x, *r;
   const float2 *p, *s, *t, *rh;

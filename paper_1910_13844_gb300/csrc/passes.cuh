@@ -33,11 +33,11 @@ struct SlotSel {
   unsigned mask;          // run slot s iff (slots[s].flags & mask) != 0 (mask 0: all)
   const float* f_default; // potential when slots == null
   int adj_default;        // adjoint flag when slots == null
-  unsigned long long* runs;  // if set: +1 per slot that ran (counted by its first work item)
-  int nslots;                // slots covered by this launch (<= kMaxLaunchSlots)
+  unsigned long long* runs;  // if set: +1 per slot that ran (counted by its first CTA)
+  int nslots;                // slots covered by this launch
 };
 
-// Upper bound on the slots one launch covers (the active list lives in shared memory).
+// Upper bound on the views of one call (slot tables are sized by it).
 constexpr int kMaxLaunchSlots = 1024;
 
 struct FxParams {
@@ -86,60 +86,15 @@ struct IxParams {
   float2* out1;                // RESID: rh (= r)
   size_t vstride;              // slot stride for in*/out* (STORE: stride of out0)
   int out_o, out_m;            // STORE: output window [out_o, out_o+out_m) of x; out rows are out_m long
-  double* partials;            // [slot][tile][4], tile = row block of PC rows
+  double* partials;            // [slot][gridDim.x][4]
   const float2* tw2;
 };
 
 __device__ __forceinline__ bool slot_runs(const SlotSel& s, int slot) {
   return !(s.slots && s.mask && !(s.slots[slot].flags & s.mask));
 }
-// Returns p unchanged but opaque to the optimiser, so loads through it are not hoisted out of
-// the work loop (keeping a whole twiddle table in registers would cut occupancy).
-template <class T>
-__device__ __forceinline__ const T* opaque(const T* p) {
-  asm volatile("" : "+l"(p));
-  return p;
-}
-
-__device__ __forceinline__ void count_run(const SlotSel& s, int tile) {
-  if (s.runs && tile == 0 && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(s.runs, 1ull);
-}
-
-// Ordered list of the slots of this launch that run (every CTA builds the same list).
-// Block size must be a multiple of 32.  Returns the number of active slots.
-__device__ __forceinline__ int build_active(const SlotSel& s, int* list, int* wsum) {
-  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  const int nth = blockDim.x * blockDim.y;
-  const int lane = tid & 31, w = tid >> 5, nw = nth >> 5;
-  const int chunk = (s.nslots + nth - 1) / nth;
-  const int beg = tid * chunk;
-  const int end = min(beg + chunk, s.nslots);
-  int c = 0;
-  for (int i = beg; i < end; ++i) c += slot_runs(s, i) ? 1 : 0;
-  int x = c;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    int v = lane < nw ? wsum[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += y;
-    }
-    wsum[lane] = v;
-  }
-  __syncthreads();
-  int off = (w > 0 ? wsum[w - 1] : 0) + x - c;
-  for (int i = beg; i < end; ++i)
-    if (slot_runs(s, i)) list[off++] = i;
-  const int total = wsum[nw - 1];
-  __syncthreads();
-  return total;
+__device__ __forceinline__ void count_run(const SlotSel& s) {
+  if (s.runs && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(s.runs, 1ull);
 }
 __device__ __forceinline__ const float* slot_f(const SlotSel& s, int slot) {
   return s.slots ? s.slots[slot].f : s.f_default;
@@ -170,8 +125,6 @@ struct Geo {
   static constexpr int PC = (T * (256 / T)) % 32 == 0 ? 256 / T : (T * (192 / T)) % 32 == 0 ? 192 / T : 32;
   static constexpr int PS = 16;                              // pencils per CTA, strided passes
   static constexpr int ZMINB = (T * PS > 256) ? 2 : ((T * PS == 256) ? 3 : 4);   // resident CTAs per SM asked of the z pass
-  static constexpr int SMINB = (T * PS > 256) ? 3 : 4;                            // ... of the FY / IY passes
-  static constexpr int CMINB = (T * PC > 256) ? 3 : 4;                            // ... of the FX / IX passes
   static constexpr int SROW = R2 + 1;                        // padded row of the contiguous exchange
   static constexpr size_t smem_contig = (size_t)PC * R1 * SROW * sizeof(float2);
   static constexpr size_t smem_strided = (size_t)L * PS * sizeof(float2);
@@ -209,152 +162,134 @@ __device__ __forceinline__ void block_sum_store(float (&acc)[NV], double* out) {
 
 // ------------------------------------------------------------------------- FX
 template <int L>
-__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, Geo<L>::CMINB) k_fx(FxParams a) {
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC) k_fx(FxParams a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
-  __shared__ int s_list[kMaxLaunchSlots];
-  __shared__ int s_ws[32];
-  const int nact = build_active(a.sel, s_list, s_ws);
+  const int slot = blockIdx.y;
+  if (!slot_runs(a.sel, slot)) return;
+  count_run(a.sel);
   const int t = threadIdx.x, p = threadIdx.y;
   const int nx = L / 2;
-  const int tiles = (a.rows + G::PC - 1) / G::PC;
-#pragma unroll 1
-  for (int item = blockIdx.x; item < nact * tiles; item += gridDim.x) {
-    const int slot = s_list[item / tiles];
-    const int tile = item % tiles;
-    count_run(a.sel, tile);
-    const int row = tile * G::PC + p;
-    const bool valid = row < a.rows;
-    const float2* tw2 = opaque(a.tw2);
-    const size_t voff = (size_t)slot * a.vstride + (size_t)row * nx;
-    const float* f = slot_f(a.sel, slot);
-    float2 v[R1];
+  const int row = blockIdx.x * G::PC + p;
+  const bool valid = row < a.rows;
+  const size_t voff = (size_t)slot * a.vstride + (size_t)row * nx;
+  const float* f = slot_f(a.sel, slot);
+  float2 v[R1];
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
-    if (valid && t < R2) {
-      float fa = 1.f, fb = 0.f, al_re = 0.f, al_im = 0.f, om_re = 0.f, om_im = 0.f;
-      bool first = false;
+  for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+  if (valid && t < R2) {
+    float fa = 1.f, fb = 0.f, al_re = 0.f, al_im = 0.f, om_re = 0.f, om_im = 0.f;
+    bool first = false;
+    if (a.mode == FX_BICG_P) {
+      const SlotDev& sd = a.sel.slots[slot];
+      first = sd.first != 0;
+      fa = (float)sd.beta.x; fb = (float)sd.beta.y;
+      om_re = (float)sd.omega.x; om_im = (float)sd.omega.y;
+    } else if (a.mode == FX_BICG_S) {
+      const SlotDev& sd = a.sel.slots[slot];
+      al_re = (float)sd.alpha.x; al_im = (float)sd.alpha.y;
+    }
+#pragma unroll
+    for (int n1 = 0; n1 < R1 / 2; ++n1) {
+      const int x = R2 * n1 + t;
+      const size_t i = voff + x;
+      float2 val = __ldg(a.src + i);
       if (a.mode == FX_BICG_P) {
-        const SlotDev& sd = a.sel.slots[slot];
-        first = sd.first != 0;
-        fa = (float)sd.beta.x; fb = (float)sd.beta.y;
-        om_re = (float)sd.omega.x; om_im = (float)sd.omega.y;
+        if (!first) {
+          // p = r + beta (p - omega v)
+          float2 pv = a.vp[i], vv = __ldg(a.vv + i);
+          float2 d = csub(pv, cmul(make_float2(om_re, om_im), vv));
+          val = cadd(val, cmul(make_float2(fa, fb), d));
+        }
+        a.vp[i] = val;
       } else if (a.mode == FX_BICG_S) {
-        const SlotDev& sd = a.sel.slots[slot];
-        al_re = (float)sd.alpha.x; al_im = (float)sd.alpha.y;
+        // s = r - alpha v
+        float2 vv = __ldg(a.vv + i);
+        val = csub(val, cmul(make_float2(al_re, al_im), vv));
+        a.vs[i] = val;
       }
-#pragma unroll
-      for (int n1 = 0; n1 < R1 / 2; ++n1) {
-        const int x = R2 * n1 + t;
-        const size_t i = voff + x;
-        float2 val = __ldg(a.src + i);
-        if (a.mode == FX_BICG_P) {
-          if (!first) {
-            // p = r + beta (p - omega v)
-            float2 pv = a.vp[i], vv = __ldg(a.vv + i);
-            float2 d = csub(pv, cmul(make_float2(om_re, om_im), vv));
-            val = cadd(val, cmul(make_float2(fa, fb), d));
-          }
-          a.vp[i] = val;
-        } else if (a.mode == FX_BICG_S) {
-          // s = r - alpha v
-          float2 vv = __ldg(a.vv + i);
-          val = csub(val, cmul(make_float2(al_re, al_im), vv));
-          a.vs[i] = val;
-        }
-        if (a.mode != FX_COPY) {
-          const float fv = __ldg(f + (size_t)row * nx + x);
-          val = cscale(val, fv);
-        }
-        v[n1] = val;
+      if (a.mode != FX_COPY) {
+        const float fv = __ldg(f + (size_t)row * nx + x);
+        val = cscale(val, fv);
       }
+      v[n1] = val;
     }
-    float2* S = sm + (size_t)p * R1 * G::SROW;
-    if (t < R2) {
-      Dft<R1, -1, R1 / 2, R1>::run(v);
+  }
+  float2* S = sm + (size_t)p * R1 * G::SROW;
+  if (t < R2) {
+    Dft<R1, -1, R1 / 2, R1>::run(v);
 #pragma unroll
-      for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], __ldg(tw2 + k1 * R2 + t));
+    for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], __ldg(a.tw2 + k1 * R2 + t));
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) S[k1 * G::SROW + t] = v[k1];
-    }
-    __syncthreads();
-    if (valid && t < R1) {
-      float2 u[R2];
+    for (int k1 = 0; k1 < R1; ++k1) S[k1 * G::SROW + t] = v[k1];
+  }
+  __syncthreads();
+  if (valid && t < R1) {
+    float2 u[R2];
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) u[n2] = S[t * G::SROW + n2];
-      Dft<R2, -1>::run(u);
-      float2* d = a.dst + (size_t)slot * a.dst_stride + (size_t)row * L;
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = S[t * G::SROW + n2];
+    Dft<R2, -1>::run(u);
+    float2* d = a.dst + (size_t)slot * a.dst_stride + (size_t)row * L;
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) d[t + R1 * k2] = u[k2];
-    }
-    __syncthreads();
+    for (int k2 = 0; k2 < R2; ++k2) d[t + R1 * k2] = u[k2];
   }
 }
 
 // ------------------------------------------------------------------------- FY / IY
 // Pencils along a strided axis; tile = 16 consecutive entries of the contiguous axis.
 template <int L, int DIR>
-__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS, Geo<L>::SMINB) k_strided(StridedParams a) {
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_strided(StridedParams a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2, P = G::PS;
   extern __shared__ float2 sm[];
-  __shared__ int s_list[kMaxLaunchSlots];
-  __shared__ int s_ws[32];
-  const int nact = build_active(a.sel, s_list, s_ws);
+  const int slot = blockIdx.y;
+  if (!slot_runs(a.sel, slot)) return;
+  count_run(a.sel);
   const int p = threadIdx.x, t = threadIdx.y;
   const int tiles_c = (a.ncont + P - 1) / P;
-  const int tiles = tiles_c * a.planes;
-#pragma unroll 1
-  for (int item = blockIdx.x; item < nact * tiles; item += gridDim.x) {
-    const int slot = s_list[item / tiles];
-    const int tile = item % tiles;
-    count_run(a.sel, tile);
-    const int plane = tile / tiles_c;
-    const int c = (tile % tiles_c) * P + p;
-    const bool valid = c < a.ncont;
-    const float2* tw = opaque(a.tw);
-    const float2* src = a.src + (size_t)slot * a.src_stride + (size_t)plane * a.src_plane + c;
-    float2 v[R1];
+  const int plane = blockIdx.x / tiles_c;
+  const int c = (blockIdx.x % tiles_c) * P + p;
+  const bool valid = c < a.ncont;
+  const float2* src = a.src + (size_t)slot * a.src_stride + (size_t)plane * a.src_plane + c;
+  float2 v[R1];
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
-    if (valid && t < R2) {
+  for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+  if (valid && t < R2) {
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) {
-        const int y = R2 * n1 + t;
-        if (DIR < 0 ? (n1 < R1 / 2) : true) v[n1] = __ldg(src + (size_t)y * a.ncont);
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const int y = R2 * n1 + t;
+      if (DIR < 0 ? (n1 < R1 / 2) : true) v[n1] = __ldg(src + (size_t)y * a.ncont);
+    }
+  }
+  if (t < R2) {
+    Dft<R1, DIR, (DIR < 0 ? R1 / 2 : R1), R1>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+      float2 w = __ldg(a.tw + k1 * t);
+      v[k1] = DIR < 0 ? cmul(v[k1], w) : cmulc(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) sm[(k1 * R2 + t) * P + p] = v[k1];
+  }
+  __syncthreads();
+  if (valid && t < R1) {
+    float2 u[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = sm[(t * R2 + n2) * P + p];
+    Dft<R2, DIR, R2, (DIR < 0 ? R2 : R2 / 2)>::run(u);
+    float2* dst = a.dst + (size_t)slot * a.dst_stride + (size_t)plane * a.dst_plane + c;
+    if (DIR < 0) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) dst[(size_t)(t + R1 * k2) * a.ncont] = u[k2];
+    } else {
+#pragma unroll
+      for (int k2 = 0; k2 < R2 / 2; ++k2) {
+        const int y = t + R1 * k2;
+        const int yo = y - a.out_o;
+        if (yo >= 0 && yo < a.out_m) dst[(size_t)yo * a.ncont] = u[k2];
       }
     }
-    if (t < R2) {
-      Dft<R1, DIR, (DIR < 0 ? R1 / 2 : R1), R1>::run(v);
-#pragma unroll
-      for (int k1 = 1; k1 < R1; ++k1) {
-        float2 w = __ldg(tw + k1 * t);
-        v[k1] = DIR < 0 ? cmul(v[k1], w) : cmulc(v[k1], w);
-      }
-#pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) sm[(k1 * R2 + t) * P + p] = v[k1];
-    }
-    __syncthreads();
-    if (valid && t < R1) {
-      float2 u[R2];
-#pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) u[n2] = sm[(t * R2 + n2) * P + p];
-      Dft<R2, DIR, R2, (DIR < 0 ? R2 : R2 / 2)>::run(u);
-      float2* dst = a.dst + (size_t)slot * a.dst_stride + (size_t)plane * a.dst_plane + c;
-      if (DIR < 0) {
-#pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) dst[(size_t)(t + R1 * k2) * a.ncont] = u[k2];
-      } else {
-#pragma unroll
-        for (int k2 = 0; k2 < R2 / 2; ++k2) {
-          const int y = t + R1 * k2;
-          const int yo = y - a.out_o;
-          if (yo >= 0 && yo < a.out_m) dst[(size_t)yo * a.ncont] = u[k2];
-        }
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -364,180 +299,163 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS, Geo<L>::ZMINB) k_z(ZPa
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2, P = G::PS;
   extern __shared__ float2 sm[];
-  __shared__ int s_list[kMaxLaunchSlots];
-  __shared__ int s_ws[32];
-  const int nact = build_active(a.sel, s_list, s_ws);
+  const int slot = blockIdx.y;
+  if (!slot_runs(a.sel, slot)) return;
+  count_run(a.sel);
   const int p = threadIdx.x, t = threadIdx.y;
   const int ncont = 2 * a.nx;
   const int tiles_c = (ncont + P - 1) / P;
-  const int tiles = tiles_c * 2 * a.ny;
+  const int ky = blockIdx.x / tiles_c;
+  const int kx = (blockIdx.x % tiles_c) * P + p;
+  const bool valid = kx < ncont;
   const size_t zstride = (size_t)(2 * a.ny) * ncont;
-#pragma unroll 1
-  for (int item = blockIdx.x; item < nact * tiles; item += gridDim.x) {
-    const int slot = s_list[item / tiles];
-    const int tile = item % tiles;
-    count_run(a.sel, tile);
-    const int ky = tile / tiles_c;
-    const int kx = (tile % tiles_c) * P + p;
-    const bool valid = kx < ncont;
-    float2* col = a.a2 + (size_t)slot * a.a2_stride + (size_t)ky * ncont + kx;
-    // forward stage 1: inputs z = R2 n1 + t, n1 < R1/2 (z < nz)
-    float2 v[R1];
+  float2* col = a.a2 + (size_t)slot * a.a2_stride + (size_t)ky * ncont + kx;
+  // forward stage 1: inputs z = R2 n1 + t, n1 < R1/2 (z < nz)
+  float2 v[R1];
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
-    if (valid && t < R2) {
+  for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+  if (valid && t < R2) {
 #pragma unroll
-      for (int n1 = 0; n1 < R1 / 2; ++n1) v[n1] = col[(size_t)(R2 * n1 + t) * zstride];
+    for (int n1 = 0; n1 < R1 / 2; ++n1) v[n1] = col[(size_t)(R2 * n1 + t) * zstride];
+  }
+  if (t < R2) {
+    Dft<R1, -1, R1 / 2, R1>::run(v);
+    // stage twiddles exp(-2 pi i t k1 / L), read two at a time from this thread's row
+    const float4* tw4 = reinterpret_cast<const float4*>(a.twa + t * R1);
+#pragma unroll
+    for (int k = 0; k < R1 / 2; ++k) {
+      const float4 w = __ldg(tw4 + k);
+      if (k > 0) v[2 * k] = cmul(v[2 * k], make_float2(w.x, w.y));
+      v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
     }
-    if (t < R2) {
-      Dft<R1, -1, R1 / 2, R1>::run(v);
-      // stage twiddles exp(-2 pi i t k1 / L), read two at a time from this thread's row
-      const float4* tw4 = reinterpret_cast<const float4*>(opaque(a.twa) + t * R1);
 #pragma unroll
-      for (int k = 0; k < R1 / 2; ++k) {
-        const float4 w = __ldg(tw4 + k);
-        if (k > 0) v[2 * k] = cmul(v[2 * k], make_float2(w.x, w.y));
-        v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
-      }
+    for (int k1 = 0; k1 < R1; ++k1) sm[(k1 * R2 + t) * P + p] = v[k1];
+  }
+  __syncthreads();
+  float2 u[R2];
+  if (t < R1) {
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) sm[(k1 * R2 + t) * P + p] = v[k1];
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = sm[(t * R2 + n2) * P + p];
+    Dft<R2, -1>::run(u);
+    // Green multiply: u[k2] holds kz = t + R1 k2; Ghat is even, read from one octant.
+    // Since nz = L/2, kz <= nz exactly when k2 < R2/2 (kz = nz only for t = 0, k2 = R2/2,
+    // where both folds agree), so the fold is known per k2 at compile time.
+    const int fx = kx <= a.nx ? kx : ncont - kx;
+    const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
+    const size_t gz = (size_t)(a.ny + 1) * (a.nx + 1);
+    const float2* glo = a.gocta + (size_t)fy * (a.nx + 1) + (valid ? fx : 0) + (size_t)t * gz;   // kz = t + R1 k2
+    const float2* ghi = a.gocta + (size_t)fy * (a.nx + 1) + (valid ? fx : 0) + (size_t)(L - t) * gz;   // L - kz
+    const size_t gstep = (size_t)R1 * gz;
+    const bool adj = slot_adj(a.sel, slot) != 0;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const float2 gv = k2 < R2 / 2 ? __ldg(glo + k2 * gstep) : __ldg(ghi - k2 * gstep);
+      u[k2] = adj ? cmulc(u[k2], gv) : cmul(u[k2], gv);
     }
-    __syncthreads();
-    float2 u[R2];
-    if (t < R1) {
+    // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
+    Dft<R2, +1>::run(u);
+    const float4* twb4 = reinterpret_cast<const float4*>(a.twb + t * R2);
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) u[n2] = sm[(t * R2 + n2) * P + p];
-      Dft<R2, -1>::run(u);
-      // Green multiply: u[k2] holds kz = t + R1 k2; Ghat is even, read from one octant.
-      // Since nz = L/2, kz <= nz exactly when k2 < R2/2 (kz = nz only for t = 0, k2 = R2/2,
-      // where both folds agree), so the fold is known per k2 at compile time.
-      const int fx = kx <= a.nx ? kx : ncont - kx;
-      const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
-      const size_t gz = (size_t)(a.ny + 1) * (a.nx + 1);
-      const float2* gocta = opaque(a.gocta);
-      const float2* glo = gocta + (size_t)fy * (a.nx + 1) + (valid ? fx : 0) + (size_t)t * gz;   // kz = t + R1 k2
-      const float2* ghi = gocta + (size_t)fy * (a.nx + 1) + (valid ? fx : 0) + (size_t)(L - t) * gz;   // L - kz
-      const size_t gstep = (size_t)R1 * gz;
-      const bool adj = slot_adj(a.sel, slot) != 0;
-#pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) {
-        const float2 gv = k2 < R2 / 2 ? __ldg(glo + k2 * gstep) : __ldg(ghi - k2 * gstep);
-        u[k2] = adj ? cmulc(u[k2], gv) : cmul(u[k2], gv);
-      }
-      // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
-      Dft<R2, +1>::run(u);
-      const float4* twb4 = reinterpret_cast<const float4*>(opaque(a.twb) + t * R2);
-#pragma unroll
-      for (int k = 0; k < R2 / 2; ++k) {
-        const float4 w = __ldg(twb4 + k);
-        if (k > 0) u[2 * k] = cmulc(u[2 * k], make_float2(w.x, w.y));
-        u[2 * k + 1] = cmulc(u[2 * k + 1], make_float2(w.z, w.w));
-      }
+    for (int k = 0; k < R2 / 2; ++k) {
+      const float4 w = __ldg(twb4 + k);
+      if (k > 0) u[2 * k] = cmulc(u[2 * k], make_float2(w.x, w.y));
+      u[2 * k + 1] = cmulc(u[2 * k + 1], make_float2(w.z, w.w));
     }
-    __syncthreads();
-    if (t < R1) {
+  }
+  __syncthreads();
+  if (t < R1) {
 #pragma unroll
-      for (int j1 = 0; j1 < R2; ++j1) sm[(j1 * R1 + t) * P + p] = u[j1];
-    }
-    __syncthreads();
-    if (valid && t < R2) {
-      float2 w[R1];
+    for (int j1 = 0; j1 < R2; ++j1) sm[(j1 * R1 + t) * P + p] = u[j1];
+  }
+  __syncthreads();
+  if (valid && t < R2) {
+    float2 w[R1];
 #pragma unroll
-      for (int m2 = 0; m2 < R1; ++m2) w[m2] = sm[(t * R1 + m2) * P + p];
-      Dft<R1, +1, R1, R1 / 2>::run(w);
-      // outputs z = t + R2 j2, keep z < nz  (j2 < R1/2)
+    for (int m2 = 0; m2 < R1; ++m2) w[m2] = sm[(t * R1 + m2) * P + p];
+    Dft<R1, +1, R1, R1 / 2>::run(w);
+    // outputs z = t + R2 j2, keep z < nz  (j2 < R1/2)
 #pragma unroll
-      for (int j2 = 0; j2 < R1 / 2; ++j2) col[(size_t)(t + R2 * j2) * zstride] = w[j2];
-    }
-    __syncthreads();
+    for (int j2 = 0; j2 < R1 / 2; ++j2) col[(size_t)(t + R2 * j2) * zstride] = w[j2];
   }
 }
 
 // ------------------------------------------------------------------------- IX
 template <int L>
-__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, Geo<L>::CMINB) k_ix(IxParams a) {
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC) k_ix(IxParams a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
-  __shared__ int s_list[kMaxLaunchSlots];
-  __shared__ int s_ws[32];
-  const int nact = build_active(a.sel, s_list, s_ws);
+  const int slot = blockIdx.y;
+  if (!slot_runs(a.sel, slot)) return;
+  count_run(a.sel);
   const int t = threadIdx.x, p = threadIdx.y;
   const int nx = L / 2;
-  const int tiles = (a.rows + G::PC - 1) / G::PC;
-#pragma unroll 1
-  for (int item = blockIdx.x; item < nact * tiles; item += gridDim.x) {
-    const int slot = s_list[item / tiles];
-    const int tile = item % tiles;
-    count_run(a.sel, tile);
-    const int row = tile * G::PC + p;
-    const bool valid = row < a.rows;
-    float2 v[R1];
+  const int row = blockIdx.x * G::PC + p;
+  const bool valid = row < a.rows;
+  float2 v[R1];
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
-    if (valid && t < R2) {
-      const float2* s = a.src + (size_t)slot * a.src_stride + (size_t)row * L;
+  for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+  if (valid && t < R2) {
+    const float2* s = a.src + (size_t)slot * a.src_stride + (size_t)row * L;
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(s + R2 * n1 + t);
-    }
-    float2* S = sm + (size_t)p * R1 * G::SROW;
-    if (t < R2) {
-      Dft<R1, +1>::run(v);
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(s + R2 * n1 + t);
+  }
+  float2* S = sm + (size_t)p * R1 * G::SROW;
+  if (t < R2) {
+    Dft<R1, +1>::run(v);
 #pragma unroll
-      for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmulc(v[k1], __ldg(a.tw2 + k1 * R2 + t));
+    for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmulc(v[k1], __ldg(a.tw2 + k1 * R2 + t));
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) S[k1 * G::SROW + t] = v[k1];
-    }
-    __syncthreads();
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    if (valid && t < R1) {
-      float2 u[R2];
+    for (int k1 = 0; k1 < R1; ++k1) S[k1 * G::SROW + t] = v[k1];
+  }
+  __syncthreads();
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  if (valid && t < R1) {
+    float2 u[R2];
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) u[n2] = S[t * G::SROW + n2];
-      Dft<R2, +1, R2, R2 / 2>::run(u);
-      const size_t voff = (size_t)slot * a.vstride + (size_t)row * nx;
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = S[t * G::SROW + n2];
+    Dft<R2, +1, R2, R2 / 2>::run(u);
+    const size_t voff = (size_t)slot * a.vstride + (size_t)row * nx;
 #pragma unroll
-      for (int k2 = 0; k2 < R2 / 2; ++k2) {
-        const int x = t + R1 * k2;
-        const float2 g = u[k2];
-        const size_t i = voff + x;
-        switch (a.mode) {
-          case IX_STORE: {
-            const int xo = x - a.out_o;
-            if (xo >= 0 && xo < a.out_m) a.out0[(size_t)slot * a.vstride + (size_t)row * a.out_m + xo] = g;
-          } break;
-          case IX_MATVEC:
-            a.out0[i] = csub(__ldg(a.in0 + i), g);
-            break;
-          case IX_BICG_V: {
-            float2 vv = csub(__ldg(a.in0 + i), g);
-            a.out0[i] = vv;
-            float2 d = cdotterm(__ldg(a.in1 + i), vv);   // conj(rh) v
-            acc[0] += d.x; acc[1] += d.y;
-          } break;
-          case IX_BICG_T: {
-            float2 ss = __ldg(a.in0 + i);
-            float2 tt = csub(ss, g);
-            a.out0[i] = tt;
-            float2 d = cdotterm(tt, ss);                  // conj(t) s
-            acc[0] += d.x; acc[1] += d.y;
-            acc[2] += tt.x * tt.x + tt.y * tt.y;
-          } break;
-          case IX_RESID: {
-            float2 b = __ldg(a.in1 + i);
-            float2 r = cadd(csub(b, __ldg(a.in0 + i)), g);   // b - (x - G f x)
-            a.out0[i] = r;
-            a.out1[i] = r;
-            acc[0] += r.x * r.x + r.y * r.y;
-            acc[1] += b.x * b.x + b.y * b.y;
-          } break;
-        }
+    for (int k2 = 0; k2 < R2 / 2; ++k2) {
+      const int x = t + R1 * k2;
+      const float2 g = u[k2];
+      const size_t i = voff + x;
+      switch (a.mode) {
+        case IX_STORE: {
+          const int xo = x - a.out_o;
+          if (xo >= 0 && xo < a.out_m) a.out0[(size_t)slot * a.vstride + (size_t)row * a.out_m + xo] = g;
+        } break;
+        case IX_MATVEC:
+          a.out0[i] = csub(__ldg(a.in0 + i), g);
+          break;
+        case IX_BICG_V: {
+          float2 vv = csub(__ldg(a.in0 + i), g);
+          a.out0[i] = vv;
+          float2 d = cdotterm(__ldg(a.in1 + i), vv);   // conj(rh) v
+          acc[0] += d.x; acc[1] += d.y;
+        } break;
+        case IX_BICG_T: {
+          float2 ss = __ldg(a.in0 + i);
+          float2 tt = csub(ss, g);
+          a.out0[i] = tt;
+          float2 d = cdotterm(tt, ss);                  // conj(t) s
+          acc[0] += d.x; acc[1] += d.y;
+          acc[2] += tt.x * tt.x + tt.y * tt.y;
+        } break;
+        case IX_RESID: {
+          float2 b = __ldg(a.in1 + i);
+          float2 r = cadd(csub(b, __ldg(a.in0 + i)), g);   // b - (x - G f x)
+          a.out0[i] = r;
+          a.out1[i] = r;
+          acc[0] += r.x * r.x + r.y * r.y;
+          acc[1] += b.x * b.x + b.y * b.y;
+        } break;
       }
     }
-    if (a.mode >= IX_BICG_V) {
-      block_sum_store<4>(acc, a.partials + ((size_t)slot * tiles + tile) * 4);
-    }
-    __syncthreads();
+  }
+  if (a.mode >= IX_BICG_V) {
+    block_sum_store<4>(acc, a.partials + ((size_t)slot * gridDim.x + blockIdx.x) * 4);
   }
 }
 
@@ -555,60 +473,35 @@ struct PassLaunch {
 template <int L>
 struct PassImpl {
   using G = Geo<L>;
-  // resident CTAs per SM of each kernel (measured once by setup()), times the SM count
-  static inline int max_ctas[5] = {0, 0, 0, 0, 0};
-  static int grid(int which, long long items) {
-    const int cap = max_ctas[which] > 0 ? max_ctas[which] : 1024;
-    return (int)(items < cap ? (items > 0 ? items : 1) : cap);
+  static void fx(const FxParams& a, int nslots, cudaStream_t st) {
+    dim3 blk(G::T, G::PC), grd((a.rows + G::PC - 1) / G::PC, nslots);
+    k_fx<L><<<grd, blk, G::smem_contig, st>>>(a);
   }
-  static void fx(const FxParams& a0, int nslots, cudaStream_t st) {
-    FxParams a = a0;
-    a.sel.nslots = nslots;
-    const long long items = (long long)nslots * ((a.rows + G::PC - 1) / G::PC);
-    k_fx<L><<<grid(0, items), dim3(G::T, G::PC), G::smem_contig, st>>>(a);
+  static void ix(const IxParams& a, int nslots, cudaStream_t st) {
+    dim3 blk(G::T, G::PC), grd((a.rows + G::PC - 1) / G::PC, nslots);
+    k_ix<L><<<grd, blk, G::smem_contig, st>>>(a);
   }
-  static void ix(const IxParams& a0, int nslots, cudaStream_t st) {
-    IxParams a = a0;
-    a.sel.nslots = nslots;
-    const long long items = (long long)nslots * ((a.rows + G::PC - 1) / G::PC);
-    k_ix<L><<<grid(1, items), dim3(G::T, G::PC), G::smem_contig, st>>>(a);
+  static void fy(const StridedParams& a, int nslots, cudaStream_t st) {
+    dim3 blk(G::PS, G::T), grd(((a.ncont + G::PS - 1) / G::PS) * a.planes, nslots);
+    k_strided<L, -1><<<grd, blk, G::smem_strided, st>>>(a);
   }
-  static void fy(const StridedParams& a0, int nslots, cudaStream_t st) {
-    StridedParams a = a0;
-    a.sel.nslots = nslots;
-    const long long items = (long long)nslots * ((a.ncont + G::PS - 1) / G::PS) * a.planes;
-    k_strided<L, -1><<<grid(2, items), dim3(G::PS, G::T), G::smem_strided, st>>>(a);
+  static void iy(const StridedParams& a, int nslots, cudaStream_t st) {
+    dim3 blk(G::PS, G::T), grd(((a.ncont + G::PS - 1) / G::PS) * a.planes, nslots);
+    k_strided<L, +1><<<grd, blk, G::smem_strided, st>>>(a);
   }
-  static void iy(const StridedParams& a0, int nslots, cudaStream_t st) {
-    StridedParams a = a0;
-    a.sel.nslots = nslots;
-    const long long items = (long long)nslots * ((a.ncont + G::PS - 1) / G::PS) * a.planes;
-    k_strided<L, +1><<<grid(3, items), dim3(G::PS, G::T), G::smem_strided, st>>>(a);
-  }
-  static void z(const ZParams& a0, int nslots, cudaStream_t st) {
-    ZParams a = a0;
-    a.sel.nslots = nslots;
-    const long long items = (long long)nslots * ((2 * a.nx + G::PS - 1) / G::PS) * (2 * a.ny);
-    k_z<L><<<grid(4, items), dim3(G::PS, G::T), G::smem_strided, st>>>(a);
+  static void z(const ZParams& a, int nslots, cudaStream_t st) {
+    dim3 blk(G::PS, G::T), grd(((2 * a.nx + G::PS - 1) / G::PS) * (2 * a.ny), nslots);
+    k_z<L><<<grd, blk, G::smem_strided, st>>>(a);
   }
   static cudaError_t setup() {
-    cudaError_t e = cudaFuncSetAttribute(k_fx<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ix<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    int nb[5] = {0, 0, 0, 0, 0};
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0], k_fx<L>, G::T * G::PC, G::smem_contig);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1], k_ix<L>, G::T * G::PC, G::smem_contig);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[2], k_strided<L, -1>, G::T * G::PS, G::smem_strided);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[3], k_strided<L, +1>, G::T * G::PS, G::smem_strided);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[4], k_z<L>, G::T * G::PS, G::smem_strided);
-    for (int i = 0; i < 5; ++i) max_ctas[i] = (nb[i] > 0 ? nb[i] : 1) * sms;
+    cudaError_t e = cudaSuccess;
+    {
+      e = cudaFuncSetAttribute(k_fx<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ix<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
+    }
     return e;
   }
   static PassLaunch table() {

@@ -45,8 +45,9 @@ struct Request {
   int status = LS_OK;
   int iters_max = 0;
   std::chrono::steady_clock::time_point t_submit, t_done;
-  double* part_h = nullptr;   // pinned residual partials [n][nb][4]
-  int nb = 0;
+  int nb = 0;                 // residual partial blocks per view
+  std::vector<float> weights; // host copies kept until the request finishes
+  std::vector<void*> ptrs;
 };
 
 struct Lane {
@@ -57,9 +58,13 @@ struct Lane {
   int cap = 0;
   size_t bytes = 0;
   std::vector<Request*> owner;   // per slot
+  double* part_h = nullptr;      // pinned [cap][kResidBlocks][4] residual partials
   bool issued = false;
   int n_iter = 0, n_resid = 0;    // host view after the last readback
 };
+
+constexpr int kResidBlocks = 32;   // residual partial blocks per view
+constexpr int kChunk = 4;          // BiCGStab iterations per round
 
 size_t plan_bytes(const ls_grid& g, int cap) {
   const size_t N = (size_t)g.nx * g.ny * g.nz;
@@ -84,10 +89,37 @@ struct ls_server {
   std::thread worker;
 
   // -------------------------------------------------------------- lanes
-  Lane* lane_for(const ls_grid& g) {
+  // a lane of grid g with a free range of n slots (s0 receives its first slot)
+  Lane* lane_for(const ls_grid& g, int n, int* s0) {
     for (Lane* l : lanes)
-      if (l->grid.nx == g.nx && l->grid.ny == g.ny && l->grid.nz == g.nz) return l;
+      if (l->grid.nx == g.nx && l->grid.ny == g.ny && l->grid.nz == g.nz) {
+        const int f = free_range(l, n);
+        if (f >= 0) {
+          *s0 = f;
+          return l;
+        }
+      }
     return nullptr;
+  }
+
+  // slots of a new lane for grid g: room for several large requests, fewer for very large grids
+  int lane_cap(const ls_grid& g, int n) const {
+    if (opt.max_views_per_grid > 0) return std::max(n, opt.max_views_per_grid);
+    const size_t N = (size_t)g.nx * g.ny * g.nz;
+    const int want = N <= ((size_t)1 << 21) ? 128 : 64;
+    return std::max(n, want);
+  }
+
+  // frees one lane without requests (the largest), returns false if none
+  bool reclaim_idle() {
+    Lane* best = nullptr;
+    for (Lane* l : lanes)
+      if (lane_idle(l) && (!best || l->bytes > best->bytes)) best = l;
+    if (!best) return false;
+    used -= best->bytes;
+    lanes.erase(std::find(lanes.begin(), lanes.end(), best));
+    destroy_lane(best);
+    return true;
   }
 
   int create_lane(const ls_grid& g, int cap, Lane** out) {
@@ -118,6 +150,10 @@ struct ls_server {
       return rc;
     }
     l->owner.assign(cap, nullptr);
+    if (cudaMallocHost(&l->part_h, (size_t)cap * kResidBlocks * 4 * sizeof(double)) != cudaSuccess) {
+      destroy_lane(l);
+      return LS_ENOMEM;
+    }
     lanes.push_back(l);
     used += l->bytes;
     *out = l;
@@ -129,6 +165,7 @@ struct ls_server {
     if (l->plan) ls_plan_destroy(l->plan);
     if (l->ev) cudaEventDestroy(l->ev);
     if (l->stream) cudaStreamDestroy(l->stream);
+    if (l->part_h) cudaFreeHost(l->part_h);
     delete l;
   }
 
@@ -154,27 +191,24 @@ struct ls_server {
       std::lock_guard<std::mutex> lk(mu);
       for (auto it = queue.begin(); it != queue.end();) {
         Request* r = *it;
-        Lane* l = lane_for(r->req.grid);
-        if (l && l->cap < r->n && lane_idle(l)) {   // rebuild a lane too small for this request
-          used -= l->bytes;
-          lanes.erase(std::find(lanes.begin(), lanes.end(), l));
-          destroy_lane(l);
-          l = nullptr;
-        }
+        int s0 = -1;
+        Lane* l = lane_for(r->req.grid, r->n, &s0);
         if (!l) {
-          int cap = std::max(r->n, opt.max_views_per_grid > 0 ? opt.max_views_per_grid : default_cap);
-          while (cap > r->n && used + plan_bytes(r->req.grid, cap) > budget) cap = std::max(r->n, cap / 2);
-          if (used + plan_bytes(r->req.grid, cap) > budget) { ++it; continue; }   // wait for memory
-          if (create_lane(r->req.grid, cap, &l) != LS_OK) {
+          const int cap = lane_cap(r->req.grid, r->n);
+          int c = cap;
+          while (c > r->n && used + plan_bytes(r->req.grid, c) > budget) c = std::max(r->n, c / 2);
+          while (used + plan_bytes(r->req.grid, c) > budget && reclaim_idle()) {
+          }
+          if (used + plan_bytes(r->req.grid, c) > budget) { ++it; continue; }   // wait for memory
+          if (create_lane(r->req.grid, c, &l) != LS_OK) {
             r->status = LS_ENOMEM;
             r->phase = PH_DONE;
             r->t_done = std::chrono::steady_clock::now();
             it = queue.erase(it);
             continue;
           }
+          s0 = 0;
         }
-        const int s0 = free_range(l, r->n);
-        if (s0 < 0) { ++it; continue; }
         r->lane = l;
         r->s0 = s0;
         for (int q = 0; q < r->n; ++q) l->owner[s0 + q] = r;
@@ -209,9 +243,9 @@ struct ls_server {
     Engine& e = P->eng;
     cudaStream_t st = l->stream;
     // plane waves into b, then x0 = b
-    std::vector<void*> ptrs(r->n);
-    for (int q = 0; q < r->n; ++q) ptrs[q] = e.vptr(V_B, r->s0 + q);
-    cudaMemcpyAsync(engine_ptr_table(P, 0) + r->s0, ptrs.data(), r->n * sizeof(void*), cudaMemcpyHostToDevice, st);
+    r->ptrs.assign(r->n, nullptr);
+    for (int q = 0; q < r->n; ++q) r->ptrs[q] = e.vptr(V_B, r->s0 + q);
+    cudaMemcpyAsync(engine_ptr_table(P, 0) + r->s0, r->ptrs.data(), r->n * sizeof(void*), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(e.kvec_d + 3 * (size_t)r->s0, r->kvec.data(), 3 * r->n * sizeof(double), cudaMemcpyHostToDevice, st);
     PlaneWaveParams a{P->nx, P->ny, P->nz, P->h, e.kvec_d + 3 * (size_t)r->s0,
                       (float2* const*)(engine_ptr_table(P, 0) + r->s0)};
@@ -251,23 +285,23 @@ struct ls_server {
     if (r->req.u_out)
       cudaMemcpyAsync(r->req.u_out, e.vptr(V_X, r->s0), (size_t)r->n * e.N * sizeof(float2),
                       cudaMemcpyDeviceToDevice, st);
-    std::vector<void*> tab(3 * r->n);
+    r->ptrs.assign(3 * r->n, nullptr);
     for (int q = 0; q < r->n; ++q) {
-      tab[q] = e.far + (size_t)(r->s0 + q) * M;
-      tab[r->n + q] = (void*)((const float2*)r->req.meas + (size_t)q * M);
-      tab[2 * r->n + q] = e.far + (size_t)(r->s0 + q) * M;
+      r->ptrs[q] = e.far + (size_t)(r->s0 + q) * M;
+      r->ptrs[r->n + q] = (void*)((const float2*)r->req.meas + (size_t)q * M);
+      r->ptrs[2 * r->n + q] = e.far + (size_t)(r->s0 + q) * M;
     }
     // tables 1 (pred), 2 (meas), 3 (res) of the lane, entries [s0, s0+n)
     for (int t = 0; t < 3; ++t)
-      cudaMemcpyAsync(engine_ptr_table(P, t + 1) + r->s0, tab.data() + t * r->n, r->n * sizeof(void*),
+      cudaMemcpyAsync(engine_ptr_table(P, t + 1) + r->s0, r->ptrs.data() + t * r->n, r->n * sizeof(void*),
                       cudaMemcpyHostToDevice, st);
-    r->nb = (int)std::min<size_t>(32, (M + 255) / 256);
+    r->nb = (int)std::min<size_t>(kResidBlocks, (M + 255) / 256);
+    double* part_d = e.partials + (size_t)r->s0 * e.maxparts * 4;
     ResidualParams rp{M, (const float2* const*)(engine_ptr_table(P, 1) + r->s0),
                       (const float2* const*)(engine_ptr_table(P, 2) + r->s0),
-                      (float2* const*)(engine_ptr_table(P, 3) + r->s0), e.partials + (size_t)r->s0 * e.maxparts * 4};
+                      (float2* const*)(engine_ptr_table(P, 3) + r->s0), part_d};
     launch_residual(rp, r->nb, r->n, st);
-    cudaMallocHost(&r->part_h, (size_t)r->n * r->nb * 4 * sizeof(double));
-    cudaMemcpyAsync(r->part_h, e.partials + (size_t)r->s0 * e.maxparts * 4, (size_t)r->n * r->nb * 4 * sizeof(double),
+    cudaMemcpyAsync(l->part_h + (size_t)r->s0 * kResidBlocks * 4, part_d, (size_t)r->n * r->nb * 4 * sizeof(double),
                     cudaMemcpyDeviceToHost, st);
     // b = G~^H r (the residual table sits in table 3 of the shifted view)
     ls_plan v = plan_slot_view(P, r->s0);
@@ -289,13 +323,15 @@ struct ls_server {
     Engine& e = P->eng;
     cudaStream_t st = l->stream;
     // weights c_q = 1/||y_q||^2 and the loss sum_q ||r_q||^2 / (2 ||y_q||^2) (eq. prob)
-    std::vector<float> w(r->n);
+    std::vector<float>& w = r->weights;
+    w.assign(r->n, 0.f);
     double loss = 0.0;
+    const double* part_h = l->part_h + (size_t)r->s0 * kResidBlocks * 4;
     for (int q = 0; q < r->n; ++q) {
       double rr = 0, yy = 0;
       for (int b = 0; b < r->nb; ++b) {
-        rr += r->part_h[((size_t)q * r->nb + b) * 4 + 0];
-        yy += r->part_h[((size_t)q * r->nb + b) * 4 + 1];
+        rr += part_h[((size_t)q * r->nb + b) * 4 + 0];
+        yy += part_h[((size_t)q * r->nb + b) * 4 + 1];
       }
       const double c = yy > 0 ? 1.0 / yy : 0.0;
       w[q] = (float)c;
@@ -303,13 +339,12 @@ struct ls_server {
     }
     if (r->req.loss) *r->req.loss = loss;
     cudaMemcpyAsync(e.weights_d + r->s0, w.data(), r->n * sizeof(float), cudaMemcpyHostToDevice, st);
-    std::vector<void*> up(r->n);
-    for (int q = 0; q < r->n; ++q) up[q] = e.ucache + (size_t)(r->s0 + q) * e.N;
-    cudaMemcpyAsync(engine_ptr_table(P, 2) + r->s0, up.data(), r->n * sizeof(void*), cudaMemcpyHostToDevice, st);
+    r->ptrs.assign(r->n, nullptr);
+    for (int q = 0; q < r->n; ++q) r->ptrs[q] = e.ucache + (size_t)(r->s0 + q) * e.N;
+    cudaMemcpyAsync(engine_ptr_table(P, 2) + r->s0, r->ptrs.data(), r->n * sizeof(void*), cudaMemcpyHostToDevice, st);
     GradParams g{e.N, r->n, (const float2* const*)(engine_ptr_table(P, 2) + r->s0), e.vptr(V_X, r->s0), e.N,
                  e.weights_d + r->s0, r->req.grad};
     launch_gradient(g, st);
-    cudaStreamSynchronize(st);   // host vectors above are about to go out of scope
     r->phase = PH_FINISHING;
   }
 
@@ -320,8 +355,7 @@ struct ls_server {
     cudaStream_t st = l->stream;
     if (l->n_resid > 0) seq_resid(P, l->cap, st);
     if (l->n_iter > 0 || l->n_resid > 0) {
-      const int chunk = 2;
-      for (int k = 0; k < chunk; ++k) cudaGraphLaunch(e.iter_graph, st);
+      for (int k = 0; k < kChunk; ++k) cudaGraphLaunch(e.iter_graph, st);
     }
     cudaMemcpyAsync(e.slots_h, e.slots_d, (size_t)l->cap * sizeof(SlotDev), cudaMemcpyDeviceToHost, st);
     cudaEventRecord(l->ev, st);
@@ -344,8 +378,6 @@ struct ls_server {
     for (Request* r : seen) {
       if (err != cudaSuccess) { fail(r, LS_ECUDA); continue; }
       if (r->phase == PH_FINISHING) {
-        cudaFreeHost(r->part_h);
-        r->part_h = nullptr;
         release(r);
         continue;
       }
