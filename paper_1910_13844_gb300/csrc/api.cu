@@ -476,6 +476,18 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   return v;
 }
 
+ls_plan* plan_clone_shared(const ls_plan* P) {
+  ls_plan* c = new ls_plan();
+  c->nx = P->nx; c->ny = P->ny; c->nz = P->nz; c->N = P->N; c->kb = P->kb; c->h = P->h; c->opt = P->opt;
+  c->mx = P->mx; c->my = P->my; c->ox = P->ox; c->oy = P->oy; c->x_gamma = P->x_gamma;
+  c->px = P->px; c->py = P->py; c->pz = P->pz;
+  c->tw_x = P->tw_x; c->tw2_x = P->tw2_x; c->tw_y = P->tw_y; c->tw_z = P->tw_z;
+  c->twa_z = P->twa_z; c->twb_z = P->twb_z;
+  c->gocta = P->gocta; c->k2hat = P->k2hat; c->p_built = P->p_built;
+  c->owns_shared = false;
+  return c;
+}
+
 int engine_solve(ls_plan* P, int nslots, cudaStream_t st) {
   Engine& e = P->eng;
   LS_CUDA_TRY(cudaMemcpyAsync(e.slots_d, e.slots_h, (size_t)nslots * sizeof(SlotDev), cudaMemcpyHostToDevice, st));
@@ -718,9 +730,11 @@ void ls_plan_destroy(ls_plan* P) {
   for (cudaEvent_t ev : P->prof.pool) cudaEventDestroy(ev);
   cudaFree(P->prof.runs_d);
   engine_release(P->eng);
-  cudaFree(P->tw_x); cudaFree(P->tw2_x); cudaFree(P->tw_y); cudaFree(P->tw_z);
-  cudaFree(P->twa_z); cudaFree(P->twb_z);
-  cudaFree(P->gocta); cudaFree(P->k2hat);
+  if (P->owns_shared) {
+    cudaFree(P->tw_x); cudaFree(P->tw2_x); cudaFree(P->tw_y); cudaFree(P->tw_z);
+    cudaFree(P->twa_z); cudaFree(P->twb_z);
+    cudaFree(P->gocta); cudaFree(P->k2hat);
+  }
   delete P;
 }
 

@@ -65,6 +65,7 @@ struct ls_plan {
   float2* gocta = nullptr;
   float2* k2hat = nullptr;
   int p_built = 0;
+  bool owns_shared = true;   // false for clones that borrow another plan's spectra and twiddles
   lsgpu::Engine eng;
   lsgpu::Profiler prof;
 };
@@ -89,6 +90,9 @@ void slot_defaults(const ls_plan* P, SlotDev& s, const float* f, int adjoint);
 int ensure_iter_graph(ls_plan* P, int nslots);
 // Shallow view of slots [s0, s0 + n) of P's engine as slots [0, n) (no ownership).
 ls_plan plan_slot_view(const ls_plan* P, int s0);
+// New plan object with its own (empty) workspace that shares P's Green spectrum, far-field
+// kernels and twiddles; P must outlive it.
+ls_plan* plan_clone_shared(const ls_plan* P);
 
 // Launch wrapper: when profiling is on, bracket the launch with an event pair.
 cudaEvent_t prof_event(ls_plan* P);

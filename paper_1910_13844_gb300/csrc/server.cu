@@ -59,7 +59,9 @@ struct Lane {
   size_t bytes = 0;
   std::vector<Request*> owner;   // per slot
   double* part_h = nullptr;      // pinned [cap][kResidBlocks][4] residual partials
+  std::vector<Request*> to_start;   // admitted, slots assigned, initialised at the next issue
   bool issued = false;
+  bool shared_plan = false;         // plan borrows the spectra of the grid's first lane
   int n_iter = 0, n_resid = 0;    // host view after the last readback
 };
 
@@ -106,15 +108,23 @@ struct ls_server {
   int lane_cap(const ls_grid& g, int n) const {
     if (opt.max_views_per_grid > 0) return std::max(n, opt.max_views_per_grid);
     const size_t N = (size_t)g.nx * g.ny * g.nz;
-    const int want = N <= ((size_t)1 << 21) ? 128 : 64;
+    const int want = N <= ((size_t)1 << 21) ? 256 : 128;
     return std::max(n, want);
   }
 
   // frees one lane without requests (the largest), returns false if none
+  bool has_clones(const Lane* b) const {
+    for (Lane* x : lanes)
+      if (x != b && x->shared_plan && x->grid.nx == b->grid.nx && x->grid.ny == b->grid.ny && x->grid.nz == b->grid.nz)
+        return true;
+    return false;
+  }
+
   bool reclaim_idle() {
     Lane* best = nullptr;
     for (Lane* l : lanes)
-      if (lane_idle(l) && (!best || l->bytes > best->bytes)) best = l;
+      if (lane_idle(l) && !l->issued && !(!l->shared_plan && has_clones(l)) && (!best || l->bytes > best->bytes))
+        best = l;
     if (!best) return false;
     used -= best->bytes;
     lanes.erase(std::find(lanes.begin(), lanes.end(), best));
@@ -131,7 +141,16 @@ struct ls_server {
     l->grid = g;
     l->cap = cap;
     l->bytes = plan_bytes(g, cap);
-    int rc = ls_plan_create(&g, 2, opt.k_b, opt.voxel, &o, &l->plan);
+    int rc = LS_OK;
+    Lane* base = nullptr;
+    for (Lane* x : lanes)
+      if (!x->shared_plan && x->grid.nx == g.nx && x->grid.ny == g.ny && x->grid.nz == g.nz) base = x;
+    if (base) {
+      l->plan = plan_clone_shared(base->plan);
+      l->shared_plan = true;
+    } else {
+      rc = ls_plan_create(&g, 2, opt.k_b, opt.voxel, &o, &l->plan);
+    }
     if (rc == LS_OK) rc = engine_reserve(l->plan, cap);
     if (rc == LS_OK) rc = engine_reserve_ucache(l->plan, cap);
     if (rc == LS_OK && cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) != cudaSuccess) rc = LS_ECUDA;
@@ -186,7 +205,6 @@ struct ls_server {
 
   // -------------------------------------------------------------- admission (worker thread)
   void admit() {
-    std::vector<Request*> take;
     {
       std::lock_guard<std::mutex> lk(mu);
       for (auto it = queue.begin(); it != queue.end();) {
@@ -212,11 +230,10 @@ struct ls_server {
         r->lane = l;
         r->s0 = s0;
         for (int q = 0; q < r->n; ++q) l->owner[s0 + q] = r;
-        take.push_back(r);
+        l->to_start.push_back(r);
         it = queue.erase(it);
       }
     }
-    for (Request* r : take) start_forward(r);
   }
 
   void fail(Request* r, int code) {
@@ -353,6 +370,8 @@ struct ls_server {
     ls_plan* P = l->plan;
     Engine& e = P->eng;
     cudaStream_t st = l->stream;
+    for (Request* r : l->to_start) start_forward(r);
+    l->to_start.clear();
     if (l->n_resid > 0) seq_resid(P, l->cap, st);
     if (l->n_iter > 0 || l->n_resid > 0) {
       for (int k = 0; k < kChunk; ++k) cudaGraphLaunch(e.iter_graph, st);
@@ -363,7 +382,7 @@ struct ls_server {
   }
 
   void process(Lane* l) {
-    cudaError_t err = cudaEventSynchronize(l->ev);
+    cudaError_t err = cudaEventQuery(l->ev);
     l->issued = false;
     Engine& e = l->plan->eng;
     if (err == cudaSuccess) err = cudaGetLastError();
@@ -401,20 +420,27 @@ struct ls_server {
     cudaSetDevice(device);
     for (;;) {
       admit();
-      bool any = false;
-      for (Lane* l : lanes) {
-        bool busy = !lane_idle(l);
-        if (busy) {
-          issue(l);
-          any = true;
+      bool progressed = false, busy = false;
+      for (size_t i = 0; i < lanes.size(); ++i) {
+        Lane* l = lanes[i];
+        if (l->issued && cudaEventQuery(l->ev) != cudaErrorNotReady) {
+          process(l);
+          progressed = true;
         }
+        if (!l->issued && !lane_idle(l)) {
+          issue(l);
+          progressed = true;
+        }
+        busy = busy || l->issued;
       }
-      for (Lane* l : lanes)
-        if (l->issued) process(l);
+      if (progressed) continue;
       std::unique_lock<std::mutex> lk(mu);
-      if (!any && queue.empty()) {
+      if (!busy && queue.empty()) {
         if (stop) break;
         cv.wait_for(lk, std::chrono::milliseconds(2));
+      } else {
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
       }
     }
   }
