@@ -459,6 +459,8 @@ def run_serving(torch, ls, n_requests, load=0.8, seed=2026, calib=12):
 
     solves = lambda r: r["views"] * (2 if r["grad"] else 1)  # noqa: E731
     reqs = serve_requests(n_requests + calib, seed)
+    for r in reqs:   # every phantom is built on the host before any timing
+        potential_for(r["shape"], r["seed"])
     srv = ls.Server(kb, ph.VOXEL_UM, tol=TOL)
     for shape in SERVE_GRIDS:   # build the lanes (plans) before measuring
         w = {"shape": shape, "views": 8, "grad": True, "seed": 0}
