@@ -163,7 +163,6 @@ struct ls_server {
       if (cudaMemcpy(e.slots_d, e.slots_h, (size_t)cap * sizeof(SlotDev), cudaMemcpyHostToDevice) != cudaSuccess)
         rc = LS_ECUDA;
     }
-    if (rc == LS_OK) rc = ensure_iter_graph(l->plan, cap);
     if (rc != LS_OK) {
       destroy_lane(l);
       return rc;
@@ -372,11 +371,20 @@ struct ls_server {
     cudaStream_t st = l->stream;
     for (Request* r : l->to_start) start_forward(r);
     l->to_start.clear();
-    if (l->n_resid > 0) seq_resid(P, l->cap, st);
-    if (l->n_iter > 0 || l->n_resid > 0) {
-      for (int k = 0; k < kChunk; ++k) cudaGraphLaunch(e.iter_graph, st);
+    // launch over the occupied slot range only (requests take slots first-fit from 0)
+    int lo = l->cap, hi = 0;
+    for (int s = 0; s < l->cap; ++s)
+      if (l->owner[s]) {
+        lo = std::min(lo, s);
+        hi = s + 1;
+      }
+    if (hi > lo) {
+      ls_plan v = plan_slot_view(P, lo);
+      if (l->n_resid > 0) seq_resid(&v, hi - lo, st);
+      if (l->n_iter > 0 || l->n_resid > 0)
+        for (int k = 0; k < kChunk; ++k) seq_iter(&v, hi - lo, st);
+      cudaMemcpyAsync(e.slots_h + lo, e.slots_d + lo, (size_t)(hi - lo) * sizeof(SlotDev), cudaMemcpyDeviceToHost, st);
     }
-    cudaMemcpyAsync(e.slots_h, e.slots_d, (size_t)l->cap * sizeof(SlotDev), cudaMemcpyDeviceToHost, st);
     cudaEventRecord(l->ev, st);
     l->issued = true;
   }
