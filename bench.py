@@ -543,6 +543,53 @@ def run_serve_mode(args):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------------------------------- reconstruction (FISTA + TV)
+def run_fista_mode(args):
+    """128^3, 60 views, ellipsoids with dn up to 0.1, FISTA with TV and positivity (Alg. 1),
+    batched solves vs one view per call, compared at their final relative errors."""
+    import time as _t
+
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1910_13844_gb300 as ls
+    from paper_1910_13844_gb300 import recon
+
+    shape, Q = (128, 128, 128), 60
+    kb = 2 * np.pi * ph.ETA_B / ph.LAMBDA_UM
+    dn = ph.random_ellipsoids(shape, count=20, rmin=4, rmax=20, dn_max=0.1)
+    dev = torch.device("cuda")
+    dnd = torch.from_numpy(dn.astype(np.float32)).to(dev)
+    f_true = torch.empty_like(dnd)
+    ls.ls_scattering_potential(dnd, ph.ETA_B, kb, f_true)
+    plan = ls.Plan(shape, kb, ph.VOXEL_UM, tol=TOL)
+    kvec = ph.cone_directions(Q, NA, ph.ETA_B) * kb
+    uin = plan.plane_waves(kvec)
+    _, y, _, _ = plan.forward(f_true, uin, want_fields=False)
+    noise = torch.from_numpy(ph.complex_normal(tuple(y.shape)).astype(np.complex64)).to(dev)
+    yn = torch.linalg.vector_norm(y.reshape(Q, -1), dim=1)
+    y = y + 0.01 * (yn / np.sqrt(2 * y[0].numel())).reshape(Q, 1, 1) * noise
+    prob = recon.Problem(plan, kvec, y)
+    f0 = torch.zeros_like(f_true)
+    _, d0 = recon.data_grad(prob, f0)
+    gamma0 = 0.5 * float(f_true.abs().max()) / float(d0.abs().max())
+    out = {"mode": "fista", "workload": "128^3, 60 views NA 0.8, 20 ellipsoids dn <= 0.1, 1% noise, TV + positivity",
+           "iterations": args.fista_iters, "gamma0": gamma0, "tau": args.tau}
+    for name, batched in (("batched", True), ("one_view_at_a_time", False)):
+        torch.cuda.synchronize()
+        t0 = _t.perf_counter()
+        st = recon.fista(prob, f0, args.fista_iters, gamma0=gamma0, tau=args.tau, tv_iters=10, batched=batched,
+                         f_true=f_true)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": round(_t.perf_counter() - t0, 2), "final_rel_error": st.history[-1][2],
+                     "final_loss": st.history[-1][1]}
+    out["speedup_batched"] = round(out["one_view_at_a_time"]["seconds"] / out["batched"]["seconds"], 3)
+    plan.close()
+    print(json.dumps(out))
+
+
 # ----------------------------------------------------------------------------- reference arm (the oracle)
 def run_reference(args):
     ws, rank, local = dist_env()
@@ -583,7 +630,13 @@ def main():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 1.0])
     ap.add_argument("--serve-requests-in-step-line", type=int, default=60)
+    ap.add_argument("--fista", action="store_true", help="FISTA/TV reconstruction benchmark instead")
+    ap.add_argument("--fista-iters", type=int, default=200)
+    ap.add_argument("--tau", type=float, default=2e-3)
     args = ap.parse_args()
+    if args.fista:
+        run_fista_mode(args)
+        return
     if args.serve:
         run_serve_mode(args)
         return
