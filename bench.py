@@ -632,7 +632,7 @@ def main():
     ap.add_argument("--serve-requests-in-step-line", type=int, default=60)
     ap.add_argument("--fista", action="store_true", help="FISTA/TV reconstruction benchmark instead")
     ap.add_argument("--fista-iters", type=int, default=200)
-    ap.add_argument("--tau", type=float, default=2e-3)
+    ap.add_argument("--tau", type=float, default=1e-6)
     args = ap.parse_args()
     if args.fista:
         run_fista_mode(args)
