@@ -96,6 +96,43 @@ __device__ __forceinline__ bool slot_runs(const SlotSel& s, int slot) {
 __device__ __forceinline__ void count_run(const SlotSel& s) {
   if (s.runs && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(s.runs, 1ull);
 }
+// Ordered list of the slots of this launch that run (every CTA builds the same list).
+// Block size must be a multiple of 32.  Returns the number of active slots.
+__device__ __forceinline__ int build_active(const SlotSel& s, int* list, int* wsum) {
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nth = blockDim.x * blockDim.y;
+  const int lane = tid & 31, w = tid >> 5, nw = nth >> 5;
+  const int chunk = (s.nslots + nth - 1) / nth;
+  const int beg = tid * chunk;
+  const int end = min(beg + chunk, s.nslots);
+  int c = 0;
+  for (int i = beg; i < end; ++i) c += slot_runs(s, i) ? 1 : 0;
+  int x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int v = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    wsum[lane] = v;
+  }
+  __syncthreads();
+  int off = (w > 0 ? wsum[w - 1] : 0) + x - c;
+  for (int i = beg; i < end; ++i)
+    if (slot_runs(s, i)) list[off++] = i;
+  const int total = wsum[nw - 1];
+  __syncthreads();
+  return total;
+}
+
 __device__ __forceinline__ const float* slot_f(const SlotSel& s, int slot) {
   return s.slots ? s.slots[slot].f : s.f_default;
 }
@@ -124,10 +161,11 @@ struct Geo {
   // rows per CTA, contiguous passes: the largest count <= 256/T that makes whole warps
   static constexpr int PC = (T * (256 / T)) % 32 == 0 ? 256 / T : (T * (192 / T)) % 32 == 0 ? 192 / T : 32;
   static constexpr int PS = 16;                              // pencils per CTA, strided passes
-  static constexpr int ZMINB = (T * PS > 256) ? 2 : ((T * PS == 256) ? 3 : 4);   // resident CTAs per SM asked of the z pass
+  static constexpr int ZMINB = (T * PS > 256) ? 1 : 2;   // resident CTAs per SM asked of the z pass
   static constexpr int SROW = R2 + 1;                        // padded row of the contiguous exchange
   static constexpr size_t smem_contig = (size_t)PC * R1 * SROW * sizeof(float2);
   static constexpr size_t smem_strided = (size_t)L * PS * sizeof(float2);
+  static constexpr size_t smem_z = (size_t)(2 * L + L) * PS * sizeof(float2);   // exchange + Ghat + 2 staging halves
 };
 
 // Warp-then-block reduction of NV float partial sums; thread 0 writes doubles to out[0..NV).
@@ -294,88 +332,131 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_strided(StridedParam
 }
 
 // ------------------------------------------------------------------------- Z
+// Asynchronous global -> shared copies (no registers held while in flight).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// One CTA owns one (ky, 16-wide kx) tile of the z pencils and loops over the views of the launch:
+// its Ghat tile is loaded into shared memory once, and the next view's pencils are copied into a
+// second staging buffer while the current view is transformed.
 template <int L>
 __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS, Geo<L>::ZMINB) k_z(ZParams a) {
   using G = Geo<L>;
-  constexpr int R1 = G::R1, R2 = G::R2, P = G::PS;
-  extern __shared__ float2 sm[];
-  const int slot = blockIdx.y;
-  if (!slot_runs(a.sel, slot)) return;
-  count_run(a.sel);
-  const int p = threadIdx.x, t = threadIdx.y;
+  constexpr int R1 = G::R1, R2 = G::R2, P = G::PS, NZ = L / 2;
+  constexpr int NT = G::T * P;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* xs = sm;                 // exchange, [L][P]
+  float2* gs = sm + L * P;         // Ghat tile, [L][P]
+  float2* stage = gs + L * P;      // two staging buffers, [2][NZ][P]
+  __shared__ int s_list[kMaxLaunchSlots];
+  __shared__ int s_ws[32];
+  const int nact = build_active(a.sel, s_list, s_ws);
+  if (nact == 0) return;
+  const int p = threadIdx.x, t = threadIdx.y, tid = t * P + p;
   const int ncont = 2 * a.nx;
   const int tiles_c = (ncont + P - 1) / P;
   const int ky = blockIdx.x / tiles_c;
-  const int kx = (blockIdx.x % tiles_c) * P + p;
+  const int kx0 = (blockIdx.x % tiles_c) * P;
+  const int kx = kx0 + p;
   const bool valid = kx < ncont;
   const size_t zstride = (size_t)(2 * a.ny) * ncont;
-  float2* col = a.a2 + (size_t)slot * a.a2_stride + (size_t)ky * ncont + kx;
-  // forward stage 1: inputs z = R2 n1 + t, n1 < R1/2 (z < nz)
-  float2 v[R1];
-#pragma unroll
-  for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
-  if (valid && t < R2) {
-#pragma unroll
-    for (int n1 = 0; n1 < R1 / 2; ++n1) v[n1] = col[(size_t)(R2 * n1 + t) * zstride];
-  }
-  if (t < R2) {
-    Dft<R1, -1, R1 / 2, R1>::run(v);
-    // stage twiddles exp(-2 pi i t k1 / L), read two at a time from this thread's row
-    const float4* tw4 = reinterpret_cast<const float4*>(a.twa + t * R1);
-#pragma unroll
-    for (int k = 0; k < R1 / 2; ++k) {
-      const float4 w = __ldg(tw4 + k);
-      if (k > 0) v[2 * k] = cmul(v[2 * k], make_float2(w.x, w.y));
-      v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
-    }
-#pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) sm[(k1 * R2 + t) * P + p] = v[k1];
-  }
-  __syncthreads();
-  float2 u[R2];
-  if (t < R1) {
-#pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) u[n2] = sm[(t * R2 + n2) * P + p];
-    Dft<R2, -1>::run(u);
-    // Green multiply: u[k2] holds kz = t + R1 k2; Ghat is even, read from one octant.
-    // Since nz = L/2, kz <= nz exactly when k2 < R2/2 (kz = nz only for t = 0, k2 = R2/2,
-    // where both folds agree), so the fold is known per k2 at compile time.
-    const int fx = kx <= a.nx ? kx : ncont - kx;
-    const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
-    const size_t gz = (size_t)(a.ny + 1) * (a.nx + 1);
-    const float2* glo = a.gocta + (size_t)fy * (a.nx + 1) + (valid ? fx : 0) + (size_t)t * gz;   // kz = t + R1 k2
-    const float2* ghi = a.gocta + (size_t)fy * (a.nx + 1) + (valid ? fx : 0) + (size_t)(L - t) * gz;   // L - kz
-    const size_t gstep = (size_t)R1 * gz;
-    const bool adj = slot_adj(a.sel, slot) != 0;
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) {
-      const float2 gv = k2 < R2 / 2 ? __ldg(glo + k2 * gstep) : __ldg(ghi - k2 * gstep);
-      u[k2] = adj ? cmulc(u[k2], gv) : cmul(u[k2], gv);
-    }
-    // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
-    Dft<R2, +1>::run(u);
-    const float4* twb4 = reinterpret_cast<const float4*>(a.twb + t * R2);
-#pragma unroll
-    for (int k = 0; k < R2 / 2; ++k) {
-      const float4 w = __ldg(twb4 + k);
-      if (k > 0) u[2 * k] = cmulc(u[2 * k], make_float2(w.x, w.y));
-      u[2 * k + 1] = cmulc(u[2 * k + 1], make_float2(w.z, w.w));
+  // Ghat for kz in [0, L) of this tile, folded into the stored octant (Ghat is even per axis)
+  const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
+  for (int i = tid; i < L * P; i += NT) {
+    const int kz = i / P, pp = i % P, kxx = kx0 + pp;
+    if (kxx < ncont) {
+      const int fz = kz <= a.nz ? kz : L - kz;
+      const int fx = kxx <= a.nx ? kxx : ncont - kxx;
+      cp_async8(&gs[i], a.gocta + ((size_t)fz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
     }
   }
-  __syncthreads();
-  if (t < R1) {
+  // staging of one view: NZ rows of P complex values, as 16-byte pairs
+  auto stage_view = [&](int slot, float2* buf) {
+    const float2* base = a.a2 + (size_t)slot * a.a2_stride + (size_t)ky * ncont + kx0;
+    for (int c = tid; c < NZ * (P / 2); c += NT) {
+      const int z = c / (P / 2), j = 2 * (c % (P / 2));
+      if (kx0 + j < ncont) cp_async16(&buf[z * P + j], base + (size_t)z * zstride + j);
+    }
+  };
+  stage_view(s_list[0], stage);
+  cp_async_commit();
+#pragma unroll 1
+  for (int iv = 0; iv < nact; ++iv) {
+    const int slot = s_list[iv];
+    if (iv + 1 < nact) stage_view(s_list[iv + 1], stage + ((iv + 1) & 1) * NZ * P);
+    cp_async_commit();
+    cp_async_wait<1>();   // every group but the newest: this view's pencils (and the Ghat tile)
+    __syncthreads();
+    count_run(a.sel);
+    const float2* stg = stage + (iv & 1) * NZ * P;
+    float2* col = a.a2 + (size_t)slot * a.a2_stride + (size_t)ky * ncont + kx;
+    // forward stage 1: inputs z = R2 n1 + t, n1 < R1/2 (z < nz)
+    float2 v[R1];
 #pragma unroll
-    for (int j1 = 0; j1 < R2; ++j1) sm[(j1 * R1 + t) * P + p] = u[j1];
-  }
-  __syncthreads();
-  if (valid && t < R2) {
-    float2 w[R1];
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+    if (t < R2) {
 #pragma unroll
-    for (int m2 = 0; m2 < R1; ++m2) w[m2] = sm[(t * R1 + m2) * P + p];
-    Dft<R1, +1, R1, R1 / 2>::run(w);
-    // outputs z = t + R2 j2, keep z < nz  (j2 < R1/2)
+      for (int n1 = 0; n1 < R1 / 2; ++n1) v[n1] = stg[(R2 * n1 + t) * P + p];
+      Dft<R1, -1, R1 / 2, R1>::run(v);
+      // stage twiddles exp(-2 pi i t k1 / L), read two at a time from this thread's row
+      const float4* tw4 = reinterpret_cast<const float4*>(a.twa + t * R1);
 #pragma unroll
-    for (int j2 = 0; j2 < R1 / 2; ++j2) col[(size_t)(t + R2 * j2) * zstride] = w[j2];
+      for (int k = 0; k < R1 / 2; ++k) {
+        const float4 w = __ldg(tw4 + k);
+        if (k > 0) v[2 * k] = cmul(v[2 * k], make_float2(w.x, w.y));
+        v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
+      }
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) xs[(k1 * R2 + t) * P + p] = v[k1];
+    }
+    __syncthreads();
+    float2 u[R2];
+    if (t < R1) {
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) u[n2] = xs[(t * R2 + n2) * P + p];
+      Dft<R2, -1>::run(u);
+      // Green multiply: u[k2] holds kz = t + R1 k2
+      const bool adj = slot_adj(a.sel, slot) != 0;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const float2 gv = gs[(t + R1 * k2) * P + p];
+        u[k2] = adj ? cmulc(u[k2], gv) : cmul(u[k2], gv);
+      }
+      // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
+      Dft<R2, +1>::run(u);
+      const float4* twb4 = reinterpret_cast<const float4*>(a.twb + t * R2);
+#pragma unroll
+      for (int k = 0; k < R2 / 2; ++k) {
+        const float4 w = __ldg(twb4 + k);
+        if (k > 0) u[2 * k] = cmulc(u[2 * k], make_float2(w.x, w.y));
+        u[2 * k + 1] = cmulc(u[2 * k + 1], make_float2(w.z, w.w));
+      }
+    }
+    __syncthreads();
+    if (t < R1) {
+#pragma unroll
+      for (int j1 = 0; j1 < R2; ++j1) xs[(j1 * R1 + t) * P + p] = u[j1];
+    }
+    __syncthreads();
+    if (valid && t < R2) {
+      float2 w[R1];
+#pragma unroll
+      for (int m2 = 0; m2 < R1; ++m2) w[m2] = xs[(t * R1 + m2) * P + p];
+      Dft<R1, +1, R1, R1 / 2>::run(w);
+      // outputs z = t + R2 j2, keep z < nz  (j2 < R1/2)
+#pragma unroll
+      for (int j2 = 0; j2 < R1 / 2; ++j2) col[(size_t)(t + R2 * j2) * zstride] = w[j2];
+    }
+    __syncthreads();
   }
 }
 
@@ -489,9 +570,11 @@ struct PassImpl {
     dim3 blk(G::PS, G::T), grd(((a.ncont + G::PS - 1) / G::PS) * a.planes, nslots);
     k_strided<L, +1><<<grd, blk, G::smem_strided, st>>>(a);
   }
-  static void z(const ZParams& a, int nslots, cudaStream_t st) {
-    dim3 blk(G::PS, G::T), grd(((2 * a.nx + G::PS - 1) / G::PS) * (2 * a.ny), nslots);
-    k_z<L><<<grd, blk, G::smem_strided, st>>>(a);
+  static void z(const ZParams& a0, int nslots, cudaStream_t st) {
+    ZParams a = a0;
+    a.sel.nslots = nslots;
+    dim3 blk(G::PS, G::T), grd(((2 * a.nx + G::PS - 1) / G::PS) * (2 * a.ny));
+    k_z<L><<<grd, blk, G::smem_z, st>>>(a);
   }
   static cudaError_t setup() {
     cudaError_t e = cudaSuccess;
@@ -500,7 +583,7 @@ struct PassImpl {
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ix<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_z);
     }
     return e;
   }
