@@ -170,6 +170,29 @@ int ls_farfield(ls_plan* plan, const float* f, int n_views, const ls_c64* const*
 int ls_farfield_adjoint(ls_plan* plan, int n_views, const ls_c64* const* r,
                         ls_c64* const* out, void* cuda_stream);
 
+/* Pupil / refocus operator P of eq. lipp2 (Sec. 3.3): a convolution on the detector applied by FFT
+ * on the detector zero-padded to 2my x 2mx, with transfer function
+ *   H(w) = 1{|w| <= k_cut} exp(i distance sqrt(k_b^2 - |w|^2))   (evanescent components dropped):
+ * an ideal pupil of cut-off k_cut (1/um, e.g. 2 pi NA / lambda) and a free-space propagation over
+ * `distance` um (e.g. the refocus from the detector plane to the sample centre, -x_gamma).
+ * Once set, ls_forward / ls_farfield return P G~ (f u) and ls_gradient / ls_farfield_adjoint apply
+ * G~^H P^H.  k_cut <= 0 removes the pupil (P = I, the default).  Synchronous; computed in float64. */
+int ls_set_pupil(ls_plan* plan, double k_cut, double distance);
+/* out[q] = P in[q] (adjoint != 0: P^H in[q]); in, out: my*mx complex64 each (may alias). */
+int ls_apply_pupil(ls_plan* plan, int n_views, const ls_c64* const* in, ls_c64* const* out, int adjoint,
+                   void* cuda_stream);
+
+/* Incident fields from their measurement on the detector plane (Sec. 3.4): for every plane z of
+ * the volume, u_in(., z) = p_z * y_in with p_hat_z(w) = exp(-i (x_gamma - z) sqrt(k_b^2 - |w|^2))
+ * (eq. propUin; evanescent components dropped), computed as a periodic convolution on the
+ * ny x nx lateral grid.  With k_in (host, 2 doubles per view: the lateral wave vector of the
+ * illumination) the tilt transfer of eq. propUin-2 is used: y_in = a exp(i x.k_in), the shifted
+ * kernel p_hat_z(w + k_in) is applied to the amplitude a and the tilt is multiplied back; k_in ==
+ * NULL propagates y_in directly.  y_in[q]: device ny*nx complex64 (the detector sampled on the
+ * volume's lateral grid at z = x_gamma); u_in[q]: device N complex64.  Computed in float64. */
+int ls_incident_field(ls_plan* plan, int n_views, const ls_c64* const* y_in, const double* k_in,
+                      ls_c64* const* u_in, void* cuda_stream);
+
 /* res[q] = pred[q] - meas[q] over `count` complex entries per view, and
  * loss_out[q] (host, may be NULL) = ||res[q]||^2 accumulated in float64. */
 int ls_residual(int n_views, size_t count, const ls_c64* const* pred, const ls_c64* const* meas,

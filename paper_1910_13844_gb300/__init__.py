@@ -27,7 +27,7 @@ __all__ = [
     "ls_scattering_potential", "ls_plane_waves", "ls_apply_green", "ls_matvec", "ls_forward", "ls_farfield",
     "ls_farfield_adjoint", "ls_residual", "ls_gradient", "ls_server_create", "ls_submit", "ls_poll",
     "ls_server_destroy", "ls_status_string", "ls_last_error", "ls_workspace_bytes", "ls_profile", "library_path",
-    "ls_matvec_noalloc", "ls_matvec_batch", "Server",
+    "ls_matvec_noalloc", "ls_matvec_batch", "Server", "ls_set_pupil", "ls_apply_pupil", "ls_incident_field",
 ]
 
 _SOFT = (LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN, LS_TIMEOUT, LS_PENDING)
@@ -143,6 +143,30 @@ def ls_apply_green(plan: int, v, out, adjoint: bool = False, stream=None) -> int
 
 def ls_matvec(plan: int, f, x, y, adjoint: bool = False, stream=None) -> int:
     return _check(_lib.ls_matvec(plan, _ptr(f), _ptr(x), _ptr(y), int(bool(adjoint)), _stream(stream)), "ls_matvec")
+
+
+def ls_set_pupil(plan: int, k_cut: float, distance: float = 0.0) -> int:
+    """Pupil of cut-off k_cut (1/um) and refocus over `distance` um applied to every far field (P of eq. lipp2)."""
+    return _check(_lib.ls_set_pupil(plan, float(k_cut), float(distance)), "ls_set_pupil")
+
+
+def ls_apply_pupil(plan: int, x, y, adjoint: bool = False, stream=None) -> int:
+    ax, n = _views(x)
+    ay, _ = _views(y)
+    return _check(_lib.ls_apply_pupil(plan, n, ax, ay, int(bool(adjoint)), _stream(stream)), "ls_apply_pupil")
+
+
+def ls_incident_field(plan: int, y_in, u_in, k_in=None, stream=None) -> int:
+    """u_in (Q, nz, ny, nx) from detector fields y_in (Q, ny, nx); k_in (Q, 2) enables tilt transfer."""
+    ay, n = _views(y_in)
+    au, _ = _views(u_in)
+    karr, kptr = None, None
+    if k_in is not None:
+        karr = np.ascontiguousarray(np.asarray(k_in, dtype=np.float64).reshape(-1, 2))
+        if karr.shape[0] != n:
+            raise ValueError("one lateral wave vector per view")
+        kptr = karr.ctypes.data_as(C.POINTER(C.c_double))
+    return _check(_lib.ls_incident_field(plan, n, ay, kptr, au, _stream(stream)), "ls_incident_field")
 
 
 def ls_matvec_batch(plan: int, f, x, y, adjoint: bool = False, stream=None) -> int:

@@ -93,6 +93,9 @@ SIGNATURES = {
     "ls_profile": (C.c_int, [_P, C.c_int, C.POINTER(ls_kernel_times)]),
     "ls_matvec_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int, _P]),
     "ls_matvec_batch": (C.c_int, [_P, _P, C.c_int, _PP, _PP, C.c_int, _P]),
+    "ls_set_pupil": (C.c_int, [_P, C.c_double, C.c_double]),
+    "ls_apply_pupil": (C.c_int, [_P, C.c_int, _PP, _PP, C.c_int, _P]),
+    "ls_incident_field": (C.c_int, [_P, C.c_int, _PP, C.POINTER(C.c_double), _PP, _P]),
 }
 
 _lib = None

@@ -555,6 +555,39 @@ void prof_resolve(ls_plan* P, bool wait) {
   pr.pending.resize(keep);
 }
 
+// far[q] <- P far[q] for the engine's detector buffers of slots [0, n) (no-op without a pupil)
+static int pupil_on_far(ls_plan* P, int n, cudaStream_t st) {
+  if (!P->pupil_h) return LS_OK;
+  double2* scratch = nullptr;
+  LS_CUDA_TRY(cudaMallocAsync((void**)&scratch, (size_t)4 * P->mx * P->my * sizeof(double2), st));
+  const size_t M = (size_t)P->mx * P->my;
+  int rc = LS_OK;
+  for (int q = 0; q < n && rc == LS_OK; ++q)
+    rc = apply_pupil_device(P, P->eng.far + q * M, P->eng.far + q * M, 0, scratch, st);
+  LS_CUDA_TRY(cudaFreeAsync(scratch, st));
+  return rc;
+}
+
+// r'_q = P^H r_q into the engine's detector buffers (returns a host table of their pointers in tab)
+static int pupil_adjoint_residuals(ls_plan* P, int n, const ls_c64* const* r, std::vector<const void*>& tab,
+                                   cudaStream_t st) {
+  tab.assign(n, nullptr);
+  const size_t M = (size_t)P->mx * P->my;
+  if (!P->pupil_h) {
+    for (int q = 0; q < n; ++q) tab[q] = r[q];
+    return LS_OK;
+  }
+  double2* scratch = nullptr;
+  LS_CUDA_TRY(cudaMallocAsync((void**)&scratch, (size_t)4 * M * sizeof(double2), st));
+  int rc = LS_OK;
+  for (int q = 0; q < n && rc == LS_OK; ++q) {
+    rc = apply_pupil_device(P, (const float2*)r[q], P->eng.far + q * M, 1, scratch, st);
+    tab[q] = P->eng.far + q * M;
+  }
+  LS_CUDA_TRY(cudaFreeAsync(scratch, st));
+  return rc;
+}
+
 static int worst_status(const Engine& e, int nslots, ls_stats* stats) {
   int worst = LS_OK;
   for (int s = 0; s < nslots; ++s) {
@@ -730,6 +763,7 @@ void ls_plan_destroy(ls_plan* P) {
   for (cudaEvent_t ev : P->prof.pool) cudaEventDestroy(ev);
   cudaFree(P->prof.runs_d);
   engine_release(P->eng);
+  cudaFree(P->pupil_h);
   if (P->owns_shared) {
     cudaFree(P->tw_x); cudaFree(P->tw2_x); cudaFree(P->tw_y); cudaFree(P->tw_z);
     cudaFree(P->twa_z); cudaFree(P->twb_z);
@@ -904,6 +938,8 @@ int ls_forward(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_i
   const int status = worst_status(e, n_views, stats);
   if (far) {
     seq_far(P, n_views, 0, st);
+    rc = pupil_on_far(P, n_views, st);
+    if (rc) return rc;
     for (int q = 0; q < n_views; ++q)
       LS_CUDA_TRY(cudaMemcpyAsync(far[q], e.far + (size_t)q * P->mx * P->my, (size_t)P->mx * P->my * sizeof(float2),
                                   cudaMemcpyDeviceToDevice, st));
@@ -930,6 +966,8 @@ int ls_farfield(ls_plan* P, const float* f, int n_views, const ls_c64* const* u,
   }
   LS_CUDA_TRY(cudaMemcpyAsync(e.slots_d, e.slots_h, (size_t)n_views * sizeof(SlotDev), cudaMemcpyHostToDevice, st));
   seq_far(P, n_views, 0, st);
+  rc = pupil_on_far(P, n_views, st);
+  if (rc) return rc;
   for (int q = 0; q < n_views; ++q)
     LS_CUDA_TRY(cudaMemcpyAsync(far[q], e.far + (size_t)q * P->mx * P->my, (size_t)P->mx * P->my * sizeof(float2),
                                 cudaMemcpyDeviceToDevice, st));
@@ -946,7 +984,10 @@ int ls_farfield_adjoint(ls_plan* P, int n_views, const ls_c64* const* r, ls_c64*
   rc = engine_reserve(P, n_views);
   if (rc) return rc;
   Engine& e = P->eng;
-  rc = engine_upload_ptrs(P, 1, (const void* const*)r, n_views, st);
+  std::vector<const void*> rt;
+  rc = pupil_adjoint_residuals(P, n_views, r, rt, st);
+  if (rc) return rc;
+  rc = engine_upload_ptrs(P, 1, rt.data(), n_views, st);
   if (rc) return rc;
   for (int q = 0; q < n_views; ++q) slot_defaults(P, e.slots_h[q], nullptr, 1);
   LS_CUDA_TRY(cudaMemcpyAsync(e.slots_d, e.slots_h, (size_t)n_views * sizeof(SlotDev), cudaMemcpyHostToDevice, st));
@@ -1027,8 +1068,11 @@ int ls_gradient(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_
   } else {
     for (int q = 0; q < n_views; ++q) uptr[q] = u_fwd[q];
   }
-  // adjoint right-hand sides b_q = G~^H r_q
-  rc = engine_upload_ptrs(P, 1, (const void* const*)residuals, n_views, st);
+  // adjoint right-hand sides b_q = G~^H P^H r_q
+  std::vector<const void*> rt;
+  rc = pupil_adjoint_residuals(P, n_views, residuals, rt, st);
+  if (rc) return rc;
+  rc = engine_upload_ptrs(P, 1, rt.data(), n_views, st);
   if (rc) return rc;
   for (int q = 0; q < n_views; ++q) slot_defaults(P, e.slots_h[q], f, 1);
   LS_CUDA_TRY(cudaMemcpyAsync(e.slots_d, e.slots_h, (size_t)n_views * sizeof(SlotDev), cudaMemcpyHostToDevice, st));

@@ -66,6 +66,7 @@ struct ls_plan {
   float2* k2hat = nullptr;
   int p_built = 0;
   bool owns_shared = true;   // false for clones that borrow another plan's spectra and twiddles
+  double2* pupil_h = nullptr; // pupil / refocus transfer function on the 2my x 2mx detector grid (ls_set_pupil)
   lsgpu::Engine eng;
   lsgpu::Profiler prof;
 };
@@ -93,6 +94,8 @@ ls_plan plan_slot_view(const ls_plan* P, int s0);
 // New plan object with its own (empty) workspace that shares P's Green spectrum, far-field
 // kernels and twiddles; P must outlive it.
 ls_plan* plan_clone_shared(const ls_plan* P);
+// P y (adjoint: P^H y) for one detector field; scratch holds 4 my mx double2
+int apply_pupil_device(ls_plan* P, const float2* in, float2* out, int adjoint, double2* scratch, cudaStream_t st);
 
 // Launch wrapper: when profiling is on, bracket the launch with an event pair.
 cudaEvent_t prof_event(ls_plan* P);

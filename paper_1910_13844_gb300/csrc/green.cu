@@ -207,6 +207,12 @@ void fft64_3d(double2* d, int Mx, int My, int Mz, int dir, cudaStream_t st) {
     k_fft64<<<(unsigned)((size_t)Mx * My), thr, 2 * Mz * sizeof(double2), st>>>(d, Mz, (size_t)Mx * My, Mx * My, 1, 0, dir);
 }
 
+// 2-D in-place float64 FFT of `planes` stacked [My][Mx] arrays.
+void fft64_2d_planes(double2* d, int Mx, int My, int planes, int dir, cudaStream_t st) {
+  k_fft64<<<(unsigned)((size_t)My * planes), 128, 2 * Mx * sizeof(double2), st>>>(d, Mx, 1, 1, 0, Mx, dir);
+  k_fft64<<<(unsigned)((size_t)Mx * planes), 128, 2 * My * sizeof(double2), st>>>(d, My, Mx, Mx, 1, (size_t)Mx * My, dir);
+}
+
 static int grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   return (int)(b > 9728 ? 9728 : (b < 1 ? 1 : b));
