@@ -26,7 +26,8 @@ void set_last_error(const char* fmt, ...) {
 
 static bool fft_length_ok(int L) {
   switch (L) {
-    case 16: case 24: case 32: case 48: case 64: case 96: case 128: case 192: case 256: case 384: return true;
+    case 16: case 24: case 32: case 48: case 64: case 96: case 128: case 144: case 192: case 256: case 288: case 384:
+      return true;
     default: return false;
   }
 }
@@ -35,33 +36,15 @@ static bool pass_for_length(int L, PassLaunch* t, cudaError_t* setup_err) {
   switch (L) {
 #define LS_CASE(LL) case LL: *t = pass_table_##LL(); *setup_err = pass_setup_##LL(); return true;
     LS_CASE(16) LS_CASE(24) LS_CASE(32) LS_CASE(48) LS_CASE(64)
-    LS_CASE(96) LS_CASE(128) LS_CASE(192) LS_CASE(256) LS_CASE(384)
+    LS_CASE(96) LS_CASE(128) LS_CASE(144) LS_CASE(192) LS_CASE(256) LS_CASE(288) LS_CASE(384)
 #undef LS_CASE
     default: return false;
   }
 }
 
-// Split L = R1 * R2 used by the passes (must match passes.cuh Radix<L>).
-static void radix_of(int L, int* R1, int* R2) {
-  switch (L) {
-    case 16: *R1 = 4; *R2 = 4; break;
-    case 24: *R1 = 4; *R2 = 6; break;
-    case 32: *R1 = 8; *R2 = 4; break;
-    case 48: *R1 = 8; *R2 = 6; break;
-    case 64: *R1 = 8; *R2 = 8; break;
-    case 96: *R1 = 8; *R2 = 12; break;
-    case 128: *R1 = 16; *R2 = 8; break;
-    case 192: *R1 = 16; *R2 = 12; break;
-    case 256: *R1 = 16; *R2 = 16; break;
-    default: *R1 = 16; *R2 = 24; break;
-  }
-}
-
 // Per-thread twiddle rows of the z pass: twa[t*R1 + k1] (t < R2) and twb[t*R2 + j1] (t < R1),
 // both exp(-2 pi i t k / L).
-static int make_z_twiddles(int L, float2** twa, float2** twb) {
-  int R1, R2;
-  radix_of(L, &R1, &R2);
+static int make_z_twiddles(int L, int R1, int R2, float2** twa, float2** twb) {
   const double pi = 3.14159265358979323846;
   std::vector<float2> a(L), b(L);
   for (int t = 0; t < R2; ++t)
@@ -82,10 +65,8 @@ static int make_z_twiddles(int L, float2** twa, float2** twb) {
 }
 
 // Twiddles computed in double on the host, rounded once to float.
-static int make_twiddles(int L, float2** tw, float2** tw2) {
+static int make_twiddles(int L, int R1, int R2, float2** tw, float2** tw2) {
   std::vector<float2> a(L), b(L);
-  int R1, R2;
-  radix_of(L, &R1, &R2);
   const double pi = 3.14159265358979323846;
   for (int j = 0; j < L; ++j) a[j] = make_float2((float)cos(-2.0 * pi * j / L), (float)sin(-2.0 * pi * j / L));
   for (int k1 = 0; k1 < R1; ++k1)
@@ -724,10 +705,10 @@ int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel, c
     delete P;
     return LS_ECUDA;
   }
-  rc = make_twiddles(L[0], &P->tw_x, &P->tw2_x);
-  if (rc == LS_OK) rc = make_twiddles(L[1], &P->tw_y, nullptr);
-  if (rc == LS_OK) rc = make_twiddles(L[2], &P->tw_z, nullptr);
-  if (rc == LS_OK) rc = make_z_twiddles(L[2], &P->twa_z, &P->twb_z);
+  rc = make_twiddles(L[0], P->px.r1, P->px.r2, &P->tw_x, &P->tw2_x);
+  if (rc == LS_OK) rc = make_twiddles(L[1], P->py.r1, P->py.r2, &P->tw_y, nullptr);
+  if (rc == LS_OK) rc = make_twiddles(L[2], P->pz.r1, P->pz.r2, &P->tw_z, nullptr);
+  if (rc == LS_OK) rc = make_z_twiddles(L[2], P->pz.r1, P->pz.r2, &P->twa_z, &P->twb_z);
   if (rc == LS_OK) {
     if (cudaMalloc(&P->gocta, (size_t)(P->nx + 1) * (P->ny + 1) * (P->nz + 1) * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&P->k2hat, (size_t)4 * P->N * sizeof(float2)) != cudaSuccess) {

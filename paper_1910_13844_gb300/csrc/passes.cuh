@@ -150,8 +150,10 @@ template <> struct Radix<48>  { static constexpr int R1 = 8,  R2 = 6;  };
 template <> struct Radix<64>  { static constexpr int R1 = 8,  R2 = 8;  };
 template <> struct Radix<96>  { static constexpr int R1 = 8,  R2 = 12; };
 template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8;  };
+template <> struct Radix<144> { static constexpr int R1 = 12, R2 = 12; };
 template <> struct Radix<192> { static constexpr int R1 = 16, R2 = 12; };
 template <> struct Radix<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct Radix<288> { static constexpr int R1 = 12, R2 = 24; };
 template <> struct Radix<384> { static constexpr int R1 = 16, R2 = 24; };
 
 template <int L>
@@ -549,6 +551,7 @@ struct PassLaunch {
   void (*ix)(const IxParams&, int nslots, cudaStream_t);
   int rows_per_cta_contig;
   int pencils_per_cta_strided;
+  int r1, r2;   // the split L = r1 * r2 of the two register stages (twiddle tables follow it)
 };
 
 template <int L>
@@ -592,6 +595,8 @@ struct PassImpl {
     t.fx = &fx; t.fy = &fy; t.iy = &iy; t.z = &z; t.ix = &ix;
     t.rows_per_cta_contig = G::PC;
     t.pencils_per_cta_strided = G::PS;
+    t.r1 = G::R1;
+    t.r2 = G::R2;
     return t;
   }
 };
@@ -607,8 +612,10 @@ LS_DECLARE_LENGTH(48)
 LS_DECLARE_LENGTH(64)
 LS_DECLARE_LENGTH(96)
 LS_DECLARE_LENGTH(128)
+LS_DECLARE_LENGTH(144)
 LS_DECLARE_LENGTH(192)
 LS_DECLARE_LENGTH(256)
+LS_DECLARE_LENGTH(288)
 LS_DECLARE_LENGTH(384)
 #undef LS_DECLARE_LENGTH
 
