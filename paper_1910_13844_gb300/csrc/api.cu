@@ -105,6 +105,33 @@ void engine_release(Engine& e) {
   e = Engine();
 }
 
+// TMA map of the engine's A2 buffers for the z pass: floats [slot][nz][2ny][4nx], box of 16 complex
+// columns x 1 row x nz planes of one slot, 128-byte swizzle.  Returns false when the driver entry
+// point is unavailable or the shape does not fit a box (the z pass then stages with cp.async).
+static bool encode_a2_map(const ls_plan* P, Engine& e) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<Encode>(fn);
+  }();
+  if (!encode || P->nz > 256 || (2 * P->nx) % 16 != 0) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)4 * P->nx, (cuuint64_t)2 * P->ny, (cuuint64_t)P->nz, (cuuint64_t)e.cap};
+  const cuuint64_t strides[3] = {(cuuint64_t)2 * P->nx * sizeof(float2),
+                                 (cuuint64_t)2 * P->nx * 2 * P->ny * sizeof(float2),
+                                 (cuuint64_t)e.a2_stride * sizeof(float2)};
+  const cuuint32_t box[4] = {32, 1, (cuuint32_t)P->nz, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return encode(&e.a2_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, e.a2, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static int max_parts(const ls_plan* P) {
   const int rows = P->ny * P->nz;
   const int ix_blocks = (rows + P->px.rows_per_cta_contig - 1) / P->px.rows_per_cta_contig;
@@ -137,8 +164,10 @@ int engine_reserve(ls_plan* P, int nslots) {
   LS_CUDA_TRY(cudaMalloc(&e.partials, (size_t)cap * e.maxparts * 4 * sizeof(double)));
   LS_CUDA_TRY(cudaMalloc(&e.slots_d, (size_t)cap * sizeof(SlotDev)));
   LS_CUDA_TRY(cudaMallocHost(&e.slots_h, (size_t)cap * sizeof(SlotDev)));
-  LS_CUDA_TRY(cudaMalloc(&e.counts_d, 4 * sizeof(int)));
-  LS_CUDA_TRY(cudaMallocHost(&e.counts_h, 4 * sizeof(int)));
+  LS_CUDA_TRY(cudaMalloc(&e.counts_d, 8 * sizeof(int)));
+  LS_CUDA_TRY(cudaMallocHost(&e.counts_h, 8 * sizeof(int)));
+  LS_CUDA_TRY(cudaMemset(e.counts_d, 0, 8 * sizeof(int)));
+  e.a2_map_ok = encode_a2_map(P, e) ? 1 : 0;
   LS_CUDA_TRY(cudaMalloc(&e.ptrs_d, (size_t)4 * cap * sizeof(void*)));
   LS_CUDA_TRY(cudaMalloc(&e.kvec_d, (size_t)3 * cap * sizeof(double)));
   LS_CUDA_TRY(cudaMalloc(&e.weights_d, (size_t)cap * sizeof(float)));
@@ -220,7 +249,11 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   timed(P, LS_K_FX, nslots, st, [&] { P->px.fx(fx, nslots, st); });
   StridedParams fy = fy_base(P, counted(P, sel, LS_K_FY), e.a1, e.a1_stride, e.a2, e.a2_stride, P->nz);
   timed(P, LS_K_FY, nslots, st, [&] { P->py.fy(fy, nslots, st); });
-  ZParams z;
+  ZParams z = {};
+  z.tmap = e.a2_map;
+  z.use_tma = e.a2_map_ok;
+  z.slot0 = e.slot0;
+  z.err = e.counts_d + 4;
   z.sel = counted(P, sel, LS_K_Z);
   z.nx = P->nx; z.ny = P->ny; z.nz = P->nz;
   z.a2 = e.a2; z.a2_stride = e.a2_stride;
@@ -452,6 +485,7 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   w.ptrs_d = e.ptrs_d + s0;
   w.kvec_d = e.kvec_d + 3 * (size_t)s0;
   w.weights_d = e.weights_d + s0;
+  w.slot0 = e.slot0 + s0;
   w.iter_graph = nullptr;
   w.cap_stream = nullptr;
   return v;
@@ -481,9 +515,13 @@ int engine_solve(ls_plan* P, int nslots, cudaStream_t st) {
   const long long max_rounds = (long long)P->opt.max_iter * (P->opt.max_restarts + 2) / chunk + 16;
   for (long long round = 0; round < max_rounds; ++round) {
     timed(P, LS_K_OTHER, nslots, st, [&] { launch_count(e.slots_d, nslots, e.counts_d, st); });
-    LS_CUDA_TRY(cudaMemcpyAsync(e.counts_h, e.counts_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    LS_CUDA_TRY(cudaMemcpyAsync(e.counts_h, e.counts_d, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
     LS_CUDA_TRY(cudaStreamSynchronize(st));
     prof_resolve(P, false);
+    if (e.counts_h[4]) {
+      set_last_error("a TMA copy of the z pass did not complete within its time limit");
+      return LS_ECUDA;
+    }
     const int n_iter = e.counts_h[0], n_resid = e.counts_h[1];
     if (n_iter == 0 && n_resid == 0) break;
     if (n_resid > 0) {

@@ -15,6 +15,9 @@ namespace lsgpu {
 enum Vec : int { V_B = 0, V_X = 1, V_R = 2, V_RH = 3, V_P = 4, V_V = 5, V_S = 6, V_T = 7, NVEC = 8 };
 
 struct Engine {
+  CUtensorMap a2_map;           // TMA map of a2 for the z pass (valid if a2_map_ok)
+  int a2_map_ok = 0;
+  int slot0 = 0;                // slot coordinate of this engine's slot 0 in a2_map (server lanes view a range)
   int cap = 0;                  // slots allocated
   size_t N = 0;
   float2* vec = nullptr;        // [NVEC][cap][N]
@@ -28,7 +31,7 @@ struct Engine {
   int maxparts = 0;
   SlotDev* slots_d = nullptr;
   SlotDev* slots_h = nullptr;   // pinned mirror
-  int* counts_d = nullptr;
+  int* counts_d = nullptr;      // [0..3] slot counts (k_count), [4] device error flag (a wait gave up)
   int* counts_h = nullptr;      // pinned
   void** ptrs_d = nullptr;      // pointer tables: [4][cap]
   double* kvec_d = nullptr;     // [cap*3]

@@ -20,6 +20,8 @@
 // transposed split), so it needs two exchanges for a forward+inverse pair.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the tensor map is encoded on the host through the runtime's driver entry point)
+
 #include "common.cuh"
 #include "dft.cuh"
 
@@ -66,6 +68,7 @@ struct StridedParams {
 };
 
 struct ZParams {
+  CUtensorMap tmap;            // A2 of all slots as floats [slot][nz][2ny][4nx], box {32, 1, nz, 1}, 128B swizzle
   SlotSel sel;
   int nx, ny, nz;              // A2 is [nz][2ny][2nx]
   float2* a2; size_t a2_stride;
@@ -73,6 +76,9 @@ struct ZParams {
   const float2* tw;
   const float2* twa;           // twa[t*R1 + k1] = exp(-2 pi i t k1 / L), t < R2 (forward split)
   const float2* twb;           // twb[t*R2 + j1] = exp(-2 pi i t j1 / L), t < R1 (transposed split)
+  int use_tma;                 // tmap is valid: the TMA-staged z pass may run
+  int slot0;                   // slot coordinate of this launch's slot 0 in tmap
+  int* err;                    // set to 1 if a wait for a TMA copy gave up (the launch's output is invalid)
 };
 
 struct IxParams {
@@ -462,6 +468,236 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS, Geo<L>::ZMINB) k_z(ZPa
   }
 }
 
+// ------------------------------------------------------------------------- Z (TMA-staged)
+// Same transform as k_z, for lengths whose pencil thread count T divides 32.  Each warp owns 32/T
+// whole columns, so both exchanges are warp-local (__syncwarp); a view costs one CTA barrier.  The
+// 16-column tile of a view is loaded by one TMA copy (128-byte swizzle, so column reads by row are
+// free of bank conflicts), transformed in place, and written back by one TMA store; the next
+// view's tile is loaded into the other buffer meanwhile.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of `bar`, giving up after about a second.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > 1000000000ull) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_addr(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5}], [%1];\n"
+               ::"l"(map), "r"(smem_addr(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+template <int L>
+struct ZW {
+  static constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2;
+  static constexpr int T = imax(R1, R2);
+  static constexpr bool ok = (32 % T) == 0;
+  static constexpr int CPW = ok ? 32 / T : 1;   // whole columns per warp (lane = t * CPW + column)
+  static constexpr int P = 16;                  // columns per CTA: one 128-byte TMA row
+  static constexpr int NW = P / CPW;
+  static constexpr int NT = 32 * NW;
+  static constexpr int NZ = L / 2;
+  static constexpr int MINB = NT >= 256 ? 2 : 512 / NT;
+  // per-column pitches (in float2) congruent to 16/CPW mod 16: the CPW columns of a half-warp then
+  // fall on disjoint banks
+  static constexpr int pitch(int n) { return n + (((16 / CPW) - n % 16) % 16 + 16) % 16; }
+  static constexpr int GP = pitch(NZ + 1);                                    // Ghat, kz folded to [0, NZ]
+  static constexpr int XP = pitch(imax(R1 * (R2 + 1), R2 * (R1 + 1)));        // exchange, padded rows
+  static constexpr int TWA = R1 + 2, TWB = R2 + 2;                            // twiddle rows (16-byte aligned)
+  static constexpr size_t stage_bytes = (size_t)NZ * P * sizeof(float2);
+  static constexpr size_t off_g = 2 * stage_bytes;
+  static constexpr size_t off_x = off_g + (size_t)P * GP * sizeof(float2);
+  static constexpr size_t off_twa = off_x + (size_t)P * XP * sizeof(float2);
+  static constexpr size_t off_twb = off_twa + (size_t)R2 * TWA * sizeof(float2);
+  static constexpr size_t off_bar = off_twb + (size_t)R1 * TWB * sizeof(float2);
+  static constexpr size_t smem = off_bar + 2 * sizeof(uint64_t) + 1024;      // + room to align the base to 1024
+};
+
+// Byte offset of element (z, c) of a [NZ][16] complex64 tile written by TMA with the 128-byte swizzle
+// (16-byte chunk index XOR row mod 8).
+__device__ __forceinline__ unsigned swz128(int z, int c) {
+  return (unsigned)(z * 128 + ((((c >> 1) ^ (z & 7)) << 4) | ((c & 1) << 3)));
+}
+
+template <bool ADJ, int R1, int R2, int L>
+__device__ __forceinline__ void green_mul(float2 (&u)[R2], const float2* gc, int t) {
+  // u[k2] holds kz = t + R1 k2; Ghat(kz) = Ghat(L - kz), stored for kz in [0, L/2]
+#pragma unroll
+  for (int k2 = 0; k2 < R2; ++k2) {
+    const float2 g = k2 < R2 / 2 ? gc[t + R1 * k2] : gc[L - R1 * k2 - t];
+    u[k2] = ADJ ? cmulc(u[k2], g) : cmul(u[k2], g);
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_constant__ ZParams a) {
+  using W = ZW<L>;
+  constexpr int R1 = W::R1, R2 = W::R2, P = W::P, NZ = W::NZ, CPW = W::CPW, T = W::T;
+  static_assert(W::ok, "k_zw needs T | 32");
+  extern __shared__ __align__(16) unsigned char zw_raw[];
+  const unsigned raw = smem_addr(zw_raw);
+  unsigned char* base = zw_raw + (((raw + 1023u) & ~1023u) - raw);
+  float2* stage = reinterpret_cast<float2*>(base);
+  float2* gs = reinterpret_cast<float2*>(base + W::off_g);
+  float2* xs = reinterpret_cast<float2*>(base + W::off_x);
+  float2* twa = reinterpret_cast<float2*>(base + W::off_twa);
+  float2* twb = reinterpret_cast<float2*>(base + W::off_twb);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);
+  __shared__ int s_list[kMaxLaunchSlots];
+  __shared__ int s_ws[32];
+  const int nact = build_active(a.sel, s_list, s_ws);
+  if (nact == 0) return;
+  const int tid = threadIdx.x;
+  const int ncont = 2 * a.nx;
+  const int tiles_c = ncont / P;
+  const int ky = blockIdx.x / tiles_c;
+  const int kx0 = (blockIdx.x % tiles_c) * P;
+  const int lane = tid & 31;
+  const int t = lane / CPW;
+  const int c = (tid >> 5) * CPW + lane % CPW;
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init_fence();
+    mbar_expect_tx(&full[0], (unsigned)W::stage_bytes);
+    tma_load_4d(stage, &a.tmap, &full[0], 2 * kx0, ky, 0, a.slot0 + s_list[0]);
+  }
+  // Ghat tile with kz folded into [0, NZ] (Ghat is even in every axis), and the stage twiddles
+  const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
+  for (int i = tid; i < (NZ + 1) * P; i += W::NT) {
+    const int kz = i / P, cc = i % P, kx = kx0 + cc;
+    const int fx = kx <= a.nx ? kx : ncont - kx;
+    gs[cc * W::GP + kz] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+  }
+  for (int i = tid; i < R1 * R2; i += W::NT) {
+    twa[(i / R1) * W::TWA + i % R1] = __ldg(a.twa + i);
+    twb[(i / R2) * W::TWB + i % R2] = __ldg(a.twb + i);
+  }
+  __syncthreads();
+  float2* xc = xs + c * W::XP;
+  const float2* gc = gs + c * W::GP;
+  // byte offset of (z = t + R2 j, c) in a tile: row base for j = 0, plus j R2 rows
+  const unsigned rb = swz128(t, c);
+  int timed_out = 0;
+  int iv = 0;
+#pragma unroll 1
+  for (; iv < nact; ++iv) {
+    const int buf = iv & 1;
+    const int slot = s_list[iv];
+    if (tid == 0 && iv + 1 < nact) {
+      bulk_wait_read_all();   // the store of view iv-1 has read the buffer that is about to be refilled
+      mbar_expect_tx(&full[buf ^ 1], (unsigned)W::stage_bytes);
+      tma_load_4d(stage + (size_t)(buf ^ 1) * NZ * P, &a.tmap, &full[buf ^ 1], 2 * kx0, ky, 0,
+                  a.slot0 + s_list[iv + 1]);
+    }
+    if (!mbar_wait(&full[buf], (unsigned)(iv >> 1) & 1u)) timed_out = 1;
+    count_run(a.sel);
+    unsigned char* sb = reinterpret_cast<unsigned char*>(stage + (size_t)buf * NZ * P);
+    float2 u[R2];
+    if (R2 == T || t < R2) {
+      // forward stage 1: inputs z = R2 n1 + t, n1 < R1/2 (z < nz)
+      float2 v[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int n1 = 0; n1 < R1 / 2; ++n1)
+        v[n1] = *reinterpret_cast<const float2*>(sb + (R2 % 8 == 0 ? rb + R2 * n1 * 128 : swz128(R2 * n1 + t, c)));
+      Dft<R1, -1, R1 / 2, R1>::run(v);
+      const float4* tw4 = reinterpret_cast<const float4*>(twa + t * W::TWA);
+#pragma unroll
+      for (int k = 0; k < R1 / 2; ++k) {
+        const float4 w = tw4[k];
+        if (k > 0) v[2 * k] = cmul(v[2 * k], make_float2(w.x, w.y));
+        v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
+      }
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) xc[k1 * (R2 + 1) + t] = v[k1];
+    }
+    __syncwarp();
+    if (R1 == T || t < R1) {
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) u[n2] = xc[t * (R2 + 1) + n2];
+      Dft<R2, -1>::run(u);
+      if (slot_adj(a.sel, slot)) green_mul<true, R1, R2, L>(u, gc, t);
+      else green_mul<false, R1, R2, L>(u, gc, t);
+      // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
+      Dft<R2, +1>::run(u);
+      const float4* tw4 = reinterpret_cast<const float4*>(twb + t * W::TWB);
+#pragma unroll
+      for (int k = 0; k < R2 / 2; ++k) {
+        const float4 w = tw4[k];
+        if (k > 0) u[2 * k] = cmulc(u[2 * k], make_float2(w.x, w.y));
+        u[2 * k + 1] = cmulc(u[2 * k + 1], make_float2(w.z, w.w));
+      }
+    }
+    __syncwarp();
+    if (R1 == T || t < R1) {
+#pragma unroll
+      for (int j1 = 0; j1 < R2; ++j1) xc[j1 * (R1 + 1) + t] = u[j1];
+    }
+    __syncwarp();
+    if (R2 == T || t < R2) {
+      float2 w[R1];
+#pragma unroll
+      for (int m2 = 0; m2 < R1; ++m2) w[m2] = xc[t * (R1 + 1) + m2];
+      Dft<R1, +1, R1, R1 / 2>::run(w);
+      // outputs z = t + R2 j2 (j2 < R1/2: z < nz), in place
+#pragma unroll
+      for (int j2 = 0; j2 < R1 / 2; ++j2)
+        *reinterpret_cast<float2*>(sb + (R2 % 8 == 0 ? rb + R2 * j2 * 128 : swz128(t + R2 * j2, c))) = w[j2];
+    }
+    fence_async_smem();
+    if (__syncthreads_or(timed_out)) break;
+    if (tid == 0) {
+      tma_store_4d(&a.tmap, sb, 2 * kx0, ky, 0, a.slot0 + slot);
+      bulk_commit();
+    }
+  }
+  if (tid == 0) {
+    bulk_wait_read_all();
+    if (iv < nact) {
+      // gave up in view iv: flag it, and give the copies still in flight into this CTA's buffers
+      // (this view's tile and the prefetch of the next one) a bounded time to land
+      atomicExch(a.err, 1);
+      mbar_wait(&full[iv & 1], (unsigned)(iv >> 1) & 1u);
+      if (iv + 1 < nact) mbar_wait(&full[(iv + 1) & 1], (unsigned)((iv + 1) >> 1) & 1u);
+    }
+  }
+}
+
 // ------------------------------------------------------------------------- IX
 template <int L>
 __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC) k_ix(IxParams a) {
@@ -576,6 +812,12 @@ struct PassImpl {
   static void z(const ZParams& a0, int nslots, cudaStream_t st) {
     ZParams a = a0;
     a.sel.nslots = nslots;
+    if constexpr (ZW<L>::ok) {
+      if (a.use_tma && (2 * a.nx) % ZW<L>::P == 0 && a.nz <= 256) {
+        k_zw<L><<<(2 * a.nx / ZW<L>::P) * (2 * a.ny), ZW<L>::NT, ZW<L>::smem, st>>>(a);
+        return;
+      }
+    }
     dim3 blk(G::PS, G::T), grd(((2 * a.nx + G::PS - 1) / G::PS) * (2 * a.ny));
     k_z<L><<<grd, blk, G::smem_z, st>>>(a);
   }
@@ -587,6 +829,8 @@ struct PassImpl {
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_z);
+      if constexpr (ZW<L>::ok)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zw<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZW<L>::smem);
     }
     return e;
   }
