@@ -208,7 +208,7 @@ __device__ __forceinline__ void block_sum_store(float (&acc)[NV], double* out) {
 
 // ------------------------------------------------------------------------- FX
 template <int L>
-__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC) k_fx(FxParams a) {
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_fx(FxParams a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
@@ -531,15 +531,15 @@ struct ZW {
   static constexpr int NT = 32 * NW;
   static constexpr int NZ = L / 2;
   static constexpr int MINB = NT >= 256 ? 2 : 512 / NT;
-  // per-column pitches (in float2) congruent to 16/CPW mod 16: the CPW columns of a half-warp then
-  // fall on disjoint banks
+  // exchange pitch per column (in float2) congruent to 16/CPW mod 16: the CPW columns of a half-warp
+  // then fall on disjoint banks; the Ghat rows [kz][P + CPW] are conflict-free for the same reason
   static constexpr int pitch(int n) { return n + (((16 / CPW) - n % 16) % 16 + 16) % 16; }
-  static constexpr int GP = pitch(NZ + 1);                                    // Ghat, kz folded to [0, NZ]
+  static constexpr int GR = P + CPW;                                          // Ghat row [kz][GR], kz folded to [0, NZ]
   static constexpr int XP = pitch(imax(R1 * (R2 + 1), R2 * (R1 + 1)));        // exchange, padded rows
   static constexpr int TWA = R1 + 2, TWB = R2 + 2;                            // twiddle rows (16-byte aligned)
   static constexpr size_t stage_bytes = (size_t)NZ * P * sizeof(float2);
   static constexpr size_t off_g = 2 * stage_bytes;
-  static constexpr size_t off_x = off_g + (size_t)P * GP * sizeof(float2);
+  static constexpr size_t off_x = off_g + (size_t)(NZ + 1) * GR * sizeof(float2);
   static constexpr size_t off_twa = off_x + (size_t)P * XP * sizeof(float2);
   static constexpr size_t off_twb = off_twa + (size_t)R2 * TWA * sizeof(float2);
   static constexpr size_t off_bar = off_twb + (size_t)R1 * TWB * sizeof(float2);
@@ -552,12 +552,12 @@ __device__ __forceinline__ unsigned swz128(int z, int c) {
   return (unsigned)(z * 128 + ((((c >> 1) ^ (z & 7)) << 4) | ((c & 1) << 3)));
 }
 
-template <bool ADJ, int R1, int R2, int L>
+template <bool ADJ, int R1, int R2, int L, int GR>
 __device__ __forceinline__ void green_mul(float2 (&u)[R2], const float2* gc, int t) {
-  // u[k2] holds kz = t + R1 k2; Ghat(kz) = Ghat(L - kz), stored for kz in [0, L/2]
+  // u[k2] holds kz = t + R1 k2; Ghat(kz) = Ghat(L - kz), stored for kz in [0, L/2] with row pitch GR
 #pragma unroll
   for (int k2 = 0; k2 < R2; ++k2) {
-    const float2 g = k2 < R2 / 2 ? gc[t + R1 * k2] : gc[L - R1 * k2 - t];
+    const float2 g = k2 < R2 / 2 ? gc[(t + R1 * k2) * GR] : gc[(L - R1 * k2 - t) * GR];
     u[k2] = ADJ ? cmulc(u[k2], g) : cmul(u[k2], g);
   }
 }
@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   for (int i = tid; i < (NZ + 1) * P; i += W::NT) {
     const int kz = i / P, cc = i % P, kx = kx0 + cc;
     const int fx = kx <= a.nx ? kx : ncont - kx;
-    gs[cc * W::GP + kz] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+    gs[kz * W::GR + cc] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
   }
   for (int i = tid; i < R1 * R2; i += W::NT) {
     twa[(i / R1) * W::TWA + i % R1] = __ldg(a.twa + i);
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   }
   __syncthreads();
   float2* xc = xs + c * W::XP;
-  const float2* gc = gs + c * W::GP;
+  const float2* gc = gs + c;
   // byte offset of (z = t + R2 j, c) in a tile: row base for j = 0, plus j R2 rows
   const unsigned rb = swz128(t, c);
   int timed_out = 0;
@@ -651,8 +651,8 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) u[n2] = xc[t * (R2 + 1) + n2];
       Dft<R2, -1>::run(u);
-      if (slot_adj(a.sel, slot)) green_mul<true, R1, R2, L>(u, gc, t);
-      else green_mul<false, R1, R2, L>(u, gc, t);
+      if (slot_adj(a.sel, slot)) green_mul<true, R1, R2, L, W::GR>(u, gc, t);
+      else green_mul<false, R1, R2, L, W::GR>(u, gc, t);
       // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
       Dft<R2, +1>::run(u);
       const float4* tw4 = reinterpret_cast<const float4*>(twb + t * W::TWB);
@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
 
 // ------------------------------------------------------------------------- IX
 template <int L>
-__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC) k_ix(IxParams a) {
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
