@@ -315,6 +315,9 @@ def run_gpu(args):
             iso_gbs[k] = round(byt / (ms_k / 1e3) / 1e9, 1)
         iso_bytes += byt
         iso_ms += ms_k
+    # BiCGStab update x += alpha p + omega s, r = s - omega t, <rh, r>: reads p, s, t, rh, x, writes x, r
+    upd_ms, _, _, upd_active = prof.get("update", (0.0, 0, 0, 0))
+    update_gbs = round(56 * N * upd_active / (upd_ms / 1e3) / 1e9, 1) if upd_ms > 0 else None
     z_ms, z_launches, _, z_active = prof["z"]
     active_per_launch = z_active / max(z_launches, 1)
     bytes_per_launch = 64 * N * active_per_launch + octant
@@ -372,6 +375,7 @@ def run_gpu(args):
             "pass_gbs": iso_gbs,
             "how": f"ls_matvec_batch over all {Q} views, 5 launches per pass, same byte model",
         },
+        "update_gbs": update_gbs,
         "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in prof.items()} if total_kernel_ms else {},
         "dominant_kernel": dominant,
         "gpu_launches": launches,

@@ -261,6 +261,8 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   z.tw = P->tw_z;
   z.twa = P->twa_z;
   z.twb = P->twb_z;
+  z.zwa = P->zwa_z;
+  z.zwb = P->zwb_z;
   timed(P, LS_K_Z, nslots, st, [&] { P->pz.z(z, nslots, st); });
   StridedParams iy = fy_base(P, counted(P, sel, LS_K_IY), e.a2, e.a2_stride, e.a1, e.a1_stride, P->nz);
   iy.src_plane = (size_t)2 * P->ny * 2 * P->nx;
@@ -469,7 +471,7 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   v.mx = P->mx; v.my = P->my; v.ox = P->ox; v.oy = P->oy; v.x_gamma = P->x_gamma;
   v.px = P->px; v.py = P->py; v.pz = P->pz;
   v.tw_x = P->tw_x; v.tw2_x = P->tw2_x; v.tw_y = P->tw_y; v.tw_z = P->tw_z;
-  v.twa_z = P->twa_z; v.twb_z = P->twb_z;
+  v.twa_z = P->twa_z; v.twb_z = P->twb_z; v.zwa_z = P->zwa_z; v.zwb_z = P->zwb_z;
   v.gocta = P->gocta; v.k2hat = P->k2hat; v.p_built = P->p_built;
   const Engine& e = P->eng;
   Engine& w = v.eng;
@@ -497,7 +499,7 @@ ls_plan* plan_clone_shared(const ls_plan* P) {
   c->mx = P->mx; c->my = P->my; c->ox = P->ox; c->oy = P->oy; c->x_gamma = P->x_gamma;
   c->px = P->px; c->py = P->py; c->pz = P->pz;
   c->tw_x = P->tw_x; c->tw2_x = P->tw2_x; c->tw_y = P->tw_y; c->tw_z = P->tw_z;
-  c->twa_z = P->twa_z; c->twb_z = P->twb_z;
+  c->twa_z = P->twa_z; c->twb_z = P->twb_z; c->zwa_z = P->zwa_z; c->zwb_z = P->zwb_z;
   c->gocta = P->gocta; c->k2hat = P->k2hat; c->p_built = P->p_built;
   c->owns_shared = false;
   return c;
@@ -748,6 +750,14 @@ int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel, c
   if (rc == LS_OK) rc = make_twiddles(L[2], P->pz.r1, P->pz.r2, &P->tw_z, nullptr);
   if (rc == LS_OK) rc = make_z_twiddles(L[2], P->pz.r1, P->pz.r2, &P->twa_z, &P->twb_z);
   if (rc == LS_OK) {
+    if (P->pz.zr1 == P->pz.r1) {
+      P->zwa_z = P->twa_z;
+      P->zwb_z = P->twb_z;
+    } else {
+      rc = make_z_twiddles(L[2], P->pz.zr1, P->pz.zr2, &P->zwa_z, &P->zwb_z);
+    }
+  }
+  if (rc == LS_OK) {
     if (cudaMalloc(&P->gocta, (size_t)(P->nx + 1) * (P->ny + 1) * (P->nz + 1) * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&P->k2hat, (size_t)4 * P->N * sizeof(float2)) != cudaSuccess) {
       set_last_error("allocation of the Green spectrum failed");
@@ -785,6 +795,7 @@ void ls_plan_destroy(ls_plan* P) {
   cudaFree(P->pupil_h);
   if (P->owns_shared) {
     cudaFree(P->tw_x); cudaFree(P->tw2_x); cudaFree(P->tw_y); cudaFree(P->tw_z);
+    if (P->zwa_z != P->twa_z) { cudaFree(P->zwa_z); cudaFree(P->zwb_z); }
     cudaFree(P->twa_z); cudaFree(P->twb_z);
     cudaFree(P->gocta); cudaFree(P->k2hat);
   }

@@ -65,6 +65,7 @@ struct ls_plan {
   lsgpu::PassLaunch px{}, py{}, pz{};
   float2 *tw_x = nullptr, *tw2_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
   float2 *twa_z = nullptr, *twb_z = nullptr;
+  float2 *zwa_z = nullptr, *zwb_z = nullptr;   // z tables for the TMA-staged split (alias twa_z/twb_z if equal)
   float2* gocta = nullptr;
   float2* k2hat = nullptr;
   int p_built = 0;

@@ -20,7 +20,7 @@ namespace lsgpu {
 
 // ------------------------------------------------------------------ update
 // x += alpha p + omega s ; r = s - omega t ; partials <rh, r>, ||r||^2
-__global__ void __launch_bounds__(256) k_update(UpdParams a) {
+__global__ void __launch_bounds__(256, 4) k_update(UpdParams a) {
   const int slot = blockIdx.y;
   if (!slot_runs(a.sel, slot)) return;
   count_run(a.sel);

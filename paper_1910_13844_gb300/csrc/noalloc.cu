@@ -112,6 +112,8 @@ extern "C" int ls_matvec_noalloc(const ls_plan* P, const float* f, const ls_c64*
   z.tw = P->tw_z;
   z.twa = P->twa_z;
   z.twb = P->twb_z;
+  z.zwa = P->zwa_z;
+  z.zwb = P->zwb_z;
   P->pz.z(z, 1, st);
 
   StridedParams iy = fy;

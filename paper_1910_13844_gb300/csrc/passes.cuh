@@ -76,6 +76,8 @@ struct ZParams {
   const float2* tw;
   const float2* twa;           // twa[t*R1 + k1] = exp(-2 pi i t k1 / L), t < R2 (forward split)
   const float2* twb;           // twb[t*R2 + j1] = exp(-2 pi i t j1 / L), t < R1 (transposed split)
+  const float2* zwa;           // the same two tables for the split of the TMA-staged pass (ZRadix)
+  const float2* zwb;
   int use_tma;                 // tmap is valid: the TMA-staged z pass may run
   int slot0;                   // slot coordinate of this launch's slot 0 in tmap
   int* err;                    // set to 1 if a wait for a TMA copy gave up (the launch's output is invalid)
@@ -520,9 +522,15 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
+// Split of the TMA-staged z pass: the pass split where its thread count divides 32, else one that does
+// (both factors even, so zero padding and cropping stay whole stages).
+template <int L> struct ZRadix { static constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2; };
+template <> struct ZRadix<96>  { static constexpr int R1 = 16, R2 = 6;  };
+template <> struct ZRadix<384> { static constexpr int R1 = 12, R2 = 32; };
+
 template <int L>
 struct ZW {
-  static constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2;
+  static constexpr int R1 = ZRadix<L>::R1, R2 = ZRadix<L>::R2;
   static constexpr int T = imax(R1, R2);
   static constexpr bool ok = (32 % T) == 0;
   static constexpr int CPW = ok ? 32 / T : 1;   // whole columns per warp (lane = t * CPW + column)
@@ -530,7 +538,7 @@ struct ZW {
   static constexpr int NW = P / CPW;
   static constexpr int NT = 32 * NW;
   static constexpr int NZ = L / 2;
-  static constexpr int MINB = NT >= 256 ? 2 : 512 / NT;
+  static constexpr int MINB = NT >= 512 ? 1 : NT >= 256 ? 2 : 512 / NT;
   // exchange pitch per column (in float2) congruent to 16/CPW mod 16: the CPW columns of a half-warp
   // then fall on disjoint banks; the Ghat rows [kz][P + CPW] are conflict-free for the same reason
   static constexpr int pitch(int n) { return n + (((16 / CPW) - n % 16) % 16 + 16) % 16; }
@@ -603,8 +611,8 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
     gs[kz * W::GR + cc] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
   }
   for (int i = tid; i < R1 * R2; i += W::NT) {
-    twa[(i / R1) * W::TWA + i % R1] = __ldg(a.twa + i);
-    twb[(i / R2) * W::TWB + i % R2] = __ldg(a.twb + i);
+    twa[(i / R1) * W::TWA + i % R1] = __ldg(a.zwa + i);
+    twb[(i / R2) * W::TWB + i % R2] = __ldg(a.zwb + i);
   }
   __syncthreads();
   float2* xc = xs + c * W::XP;
@@ -788,6 +796,7 @@ struct PassLaunch {
   int rows_per_cta_contig;
   int pencils_per_cta_strided;
   int r1, r2;   // the split L = r1 * r2 of the two register stages (twiddle tables follow it)
+  int zr1, zr2; // the split of the TMA-staged z pass
 };
 
 template <int L>
@@ -841,6 +850,8 @@ struct PassImpl {
     t.pencils_per_cta_strided = G::PS;
     t.r1 = G::R1;
     t.r2 = G::R2;
+    t.zr1 = ZRadix<L>::R1;
+    t.zr2 = ZRadix<L>::R2;
     return t;
   }
 };

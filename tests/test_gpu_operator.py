@@ -10,6 +10,9 @@ from gpu_common import H, KB, potential, rel, to_dev, torch_and_lib
 # (nz, ny, nx): cubic, non-cubic with ragged CTA tiles (2nx = 24, 48; rows not a multiple of the tile),
 # and a config-sized non-cubic grid
 SHAPES = [(8, 8, 8), (12, 16, 24), (16, 8, 12), (32, 32, 32), (24, 48, 16), (96, 128, 128)]
+# every z transform length of the pass table: 96 and 384 run the TMA-staged z pass with their own
+# split (16 x 6, 12 x 32), 144 and 288 the cp.async-staged one
+Z_LENGTHS = [(48, 24, 16), (192, 16, 16), (72, 16, 16), (144, 16, 32)]
 
 
 @pytest.mark.gpu
@@ -28,7 +31,7 @@ def test_green_spectrum_matches_oracle(shape):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", SHAPES + Z_LENGTHS)
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_green_operator_and_matvec_match_oracle(shape, adjoint):
     torch, ls = torch_and_lib()
