@@ -162,6 +162,14 @@ int ls_matvec_noalloc(const ls_plan* plan, const float* f, const ls_c64* x, ls_c
 int ls_forward(ls_plan* plan, const float* f, int n_views, const ls_c64* const* u_in,
                ls_c64* const* u_out, ls_c64* const* far, ls_stats* stats, void* cuda_stream);
 
+/* ls_forward with initial guesses: BiCGStab for view q starts from x0[q] (device, N complex64
+ * each; may alias u_out[q]) instead of u_in[q].  Used to warm-start the forward solves of one
+ * reconstruction iteration from the fields of the previous one (Alg. 1 evaluates the model at
+ * potentials that change little between iterations); the paper states no initial guess. */
+int ls_forward_warm(ls_plan* plan, const float* f, int n_views, const ls_c64* const* u_in,
+                    const ls_c64* const* x0, ls_c64* const* u_out, ls_c64* const* far, ls_stats* stats,
+                    void* cuda_stream);
+
 /* far[q] = G~ (f .* u[q]) (eq. Gtild-1, midpoint rule, exact per-slice 2-D convolutions). */
 int ls_farfield(ls_plan* plan, const float* f, int n_views, const ls_c64* const* u,
                 ls_c64* const* far, void* cuda_stream);
@@ -181,6 +189,15 @@ int ls_set_pupil(ls_plan* plan, double k_cut, double distance);
 /* out[q] = P in[q] (adjoint != 0: P^H in[q]); in, out: my*mx complex64 each (may alias). */
 int ls_apply_pupil(ls_plan* plan, int n_views, const ls_c64* const* in, ls_c64* const* out, int adjoint,
                    void* cuda_stream);
+
+/* x = prox_{lam TV + i_{>=0}}(z) = argmin_{x >= 0} 0.5 ||x - z||^2 + lam TV(x), the prox step of
+ * Alg. 1 (Sec. 4.2) with the isotropic total variation (forward differences, zero difference on the
+ * last plane of each axis), evaluated by `iters` iterations of the fast gradient projection method
+ * on the dual (step 1/(12 lam)), as the paper does.  z, x: device float [nz][ny][nx] that must not
+ * overlap when lam > 0; work: device scratch of 6*nx*ny*nz floats, or NULL to allocate it on the
+ * stream.  lam <= 0 gives max(z, 0) (then z and x may alias).  Asynchronous on cuda_stream. */
+int ls_prox_tv(const ls_grid* grid, const float* z, float* x, double lam, int iters, float* work,
+               void* cuda_stream);
 
 /* Incident fields from their measurement on the detector plane (Sec. 3.4): for every plane z of
  * the volume, u_in(., z) = p_z * y_in with p_hat_z(w) = exp(-i (x_gamma - z) sqrt(k_b^2 - |w|^2))

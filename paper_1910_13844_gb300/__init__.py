@@ -28,6 +28,7 @@ __all__ = [
     "ls_farfield_adjoint", "ls_residual", "ls_gradient", "ls_server_create", "ls_submit", "ls_poll",
     "ls_server_destroy", "ls_status_string", "ls_last_error", "ls_workspace_bytes", "ls_profile", "library_path",
     "ls_matvec_noalloc", "ls_matvec_batch", "Server", "ls_set_pupil", "ls_apply_pupil", "ls_incident_field",
+    "ls_forward_warm", "ls_prox_tv",
 ]
 
 _SOFT = (LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN, LS_TIMEOUT, LS_PENDING)
@@ -193,6 +194,30 @@ def ls_forward(plan: int, f, u_in, u_out=None, far=None, stream=None):
     st = (ls_stats * n)()
     code = _check(_lib.ls_forward(plan, _ptr(f), n, a_in, a_out, a_far, st, _stream(stream)), "ls_forward")
     return code, [s.as_dict() for s in st]
+
+
+def ls_forward_warm(plan: int, f, u_in, x0, u_out=None, far=None, stream=None):
+    """ls_forward starting BiCGStab from x0 (Q, nz, ny, nx); x0 may be u_out.  Returns (status, stats)."""
+    a_in, n = _views(u_in)
+    a_x0, n0 = _views(x0)
+    if n0 != n:
+        raise ValueError("one initial guess per view")
+    a_out, _ = _views(u_out)
+    a_far, _ = _views(far)
+    st = (ls_stats * n)()
+    code = _check(_lib.ls_forward_warm(plan, _ptr(f), n, a_in, a_x0, a_out, a_far, st, _stream(stream)),
+                  "ls_forward_warm")
+    return code, [s.as_dict() for s in st]
+
+
+def ls_prox_tv(z, x, lam: float, iters: int = 20, work=None, stream=None) -> int:
+    """x = prox of lam TV + i_{>=0} at z (float32 CUDA tensors (nz, ny, nx)) by `iters` FGP iterations."""
+    if z.dim() != 3 or z.shape != x.shape:
+        raise ValueError("z and x must be (nz, ny, nx) tensors of the same shape")
+    nz, ny, nx = z.shape
+    g = ls_grid(nx, ny, nz)
+    return _check(_lib.ls_prox_tv(C.byref(g), _ptr(z), _ptr(x), float(lam), int(iters),
+                                  _ptr(work) if work is not None else None, _stream(stream)), "ls_prox_tv")
 
 
 def ls_farfield(plan: int, f, u, far, stream=None) -> int:

@@ -939,21 +939,26 @@ int ls_matvec_batch(ls_plan* P, const float* f, int n_views, const ls_c64* const
   return LS_OK;
 }
 
-// Copy the caller's right-hand sides into slots [0, n) (b and x0 = b) and set the slot states.
-static int load_rhs(ls_plan* P, const float* f, int n, const ls_c64* const* rhs, int adjoint, cudaStream_t st) {
+// Copy the caller's right-hand sides into slots [0, n) (b, and x0 = b unless initial guesses are given)
+// and set the slot states.
+static int load_rhs(ls_plan* P, const float* f, int n, const ls_c64* const* rhs, int adjoint, cudaStream_t st,
+                    const ls_c64* const* x0 = nullptr) {
   Engine& e = P->eng;
   for (int q = 0; q < n; ++q) {
     LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_B, q), rhs[q], e.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_X, q), rhs[q], e.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_X, q), x0 ? x0[q] : rhs[q], e.N * sizeof(float2),
+                                cudaMemcpyDeviceToDevice, st));
   }
   for (int q = 0; q < n; ++q) slot_defaults(P, e.slots_h[q], f, adjoint);
   return LS_OK;
 }
 
-int ls_forward(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_in, ls_c64* const* u_out,
-               ls_c64* const* far, ls_stats* stats, void* stream) {
+static int forward_impl(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_in,
+                        const ls_c64* const* x0, ls_c64* const* u_out, ls_c64* const* far, ls_stats* stats,
+                        void* stream) {
   if (!P || !f || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
   int rc = check_views(n_views, (const void* const*)u_in, "u_in", false);
+  if (!rc && x0) rc = check_views(n_views, (const void* const*)x0, "x0", false);
   if (!rc) rc = check_views(n_views, (const void* const*)u_out, "u_out", true);
   if (!rc) rc = check_views(n_views, (const void* const*)far, "far", true);
   if (rc) return rc;
@@ -961,7 +966,7 @@ int ls_forward(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_i
   rc = engine_reserve(P, n_views);
   if (rc) return rc;
   Engine& e = P->eng;
-  rc = load_rhs(P, f, n_views, u_in, 0, st);
+  rc = load_rhs(P, f, n_views, u_in, 0, st, x0);
   if (rc) return rc;
   rc = engine_solve(P, n_views, st);
   if (rc) return rc;
@@ -979,6 +984,17 @@ int ls_forward(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_i
       LS_CUDA_TRY(cudaMemcpyAsync(u_out[q], e.vptr(V_X, q), e.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
   LS_CUDA_TRY(cudaGetLastError());
   return status;
+}
+
+int ls_forward(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_in, ls_c64* const* u_out,
+               ls_c64* const* far, ls_stats* stats, void* stream) {
+  return forward_impl(P, f, n_views, u_in, nullptr, u_out, far, stats, stream);
+}
+
+int ls_forward_warm(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_in, const ls_c64* const* x0,
+                    ls_c64* const* u_out, ls_c64* const* far, ls_stats* stats, void* stream) {
+  if (!x0) { set_last_error("x0 is null (use ls_forward)"); return LS_EINVAL; }
+  return forward_impl(P, f, n_views, u_in, x0, u_out, far, stats, stream);
 }
 
 int ls_farfield(ls_plan* P, const float* f, int n_views, const ls_c64* const* u, ls_c64* const* far, void* stream) {

@@ -7,8 +7,10 @@ gamma_k = gamma_0 / sqrt(k), optional random view subsets per iteration
 (Alg. 1 line 5), and the proximal operator of gamma tau TV + i_{>=0} evaluated
 by the fast gradient projection method (FGP) on the dual of isotropic TV.
 The data-term gradient (Alg. 1 line 6) comes from the CUDA library, batched
-over the selected views (or one view per call, for comparison); the TV prox
-and the FISTA updates are element-wise tensor operations on the device.
+over the selected views (or one view per call, for comparison), with the forward
+solves optionally warm-started from the previous iteration's fields; the TV prox
+is the library's fused FGP kernels; the FISTA updates are element-wise tensor
+operations on the device.
 
 Reading of Alg. 1: the gradient is evaluated at the extrapolated point v^k
 (standard FISTA), where the listing writes f^k.
@@ -22,48 +24,15 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import ls_forward, ls_gradient, ls_plane_waves, ls_residual
+from . import ls_forward, ls_forward_warm, ls_gradient, ls_plane_waves, ls_prox_tv, ls_residual
 
 
 # ------------------------------------------------------------------ TV prox (FGP)
-def _grad3(x):
-    """Forward differences with Neumann boundary, stacked (3, nz, ny, nx)."""
-    g = torch.zeros((3,) + x.shape, dtype=x.dtype, device=x.device)
-    g[0, :-1] = x[1:] - x[:-1]
-    g[1, :, :-1] = x[:, 1:] - x[:, :-1]
-    g[2, :, :, :-1] = x[:, :, 1:] - x[:, :, :-1]
-    return g
-
-
-def _div3(p):
-    """Negative adjoint of _grad3."""
-    d = torch.zeros(p.shape[1:], dtype=p.dtype, device=p.device)
-    d[:-1] += p[0, :-1]
-    d[1:] -= p[0, :-1]
-    d[:, :-1] += p[1, :, :-1]
-    d[:, 1:] -= p[1, :, :-1]
-    d[:, :, :-1] += p[2, :, :, :-1]
-    d[:, :, 1:] -= p[2, :, :, :-1]
-    return d
-
-
 def prox_tv_nonneg(z: torch.Tensor, lam: float, iters: int = 20) -> torch.Tensor:
-    """argmin_x 0.5 ||x - z||^2 + lam TV(x) + i_{>=0}(x) by FGP (Beck and Teboulle 2009)."""
-    if lam <= 0:
-        return z.clamp_min(0.0)
-    p = torch.zeros((3,) + z.shape, dtype=z.dtype, device=z.device)
-    r = p.clone()
-    t = 1.0
-    step = 1.0 / (12.0 * lam)          # 1 / (lam * ||grad||^2), ||grad||^2 <= 12 in 3-D
-    for _ in range(iters):
-        x = (z + lam * _div3(r)).clamp_min(0.0)
-        pn = r + step * _grad3(x)
-        norm = pn.pow(2).sum(dim=0).sqrt().clamp_min(1.0)
-        pn = pn / norm
-        tn = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
-        r = pn + ((t - 1.0) / tn) * (pn - p)
-        p, t = pn, tn
-    return (z + lam * _div3(p)).clamp_min(0.0)
+    """argmin_x 0.5 ||x - z||^2 + lam TV(x) + i_{>=0}(x) by FGP (Beck and Teboulle 2009), in the library."""
+    x = torch.empty_like(z)
+    ls_prox_tv(z.contiguous(), x, lam, iters)
+    return x
 
 
 # ------------------------------------------------------------------ data term
@@ -80,8 +49,13 @@ class Problem:
             self.weights = 1.0 / yy
 
 
-def data_grad(prob: Problem, f: torch.Tensor, views=None, batched: bool = True):
-    """(loss, gradient) of the data term over `views` (all if None): batched, or one view per call."""
+def data_grad(prob: Problem, f: torch.Tensor, views=None, batched: bool = True, warm: dict | None = None,
+              stats: list | None = None):
+    """(loss, gradient) of the data term over `views` (all if None): batched, or one view per call.
+
+    warm: a dict view -> field kept across calls; views found there start BiCGStab from that field
+    (ls_forward_warm) and every view's new field is stored back.  stats: list that receives the
+    per-view solver statistics of the forward solves."""
     Q = prob.kvec.shape[0]
     idx = list(range(Q)) if views is None else list(views)
     plan = prob.plan
@@ -94,7 +68,17 @@ def data_grad(prob: Problem, f: torch.Tensor, views=None, batched: bool = True):
         ls_plane_waves(plan.handle, k, uin)
         u = plan.field(len(g))
         far = plan.detector(len(g))
-        ls_forward(plan.handle, f, uin, u, far)
+        if warm is not None and all(q in warm for q in g):
+            for i, q in enumerate(g):
+                u[i].copy_(warm[q])
+            _, st = ls_forward_warm(plan.handle, f, uin, u, u, far)
+        else:
+            _, st = ls_forward(plan.handle, f, uin, u, far)
+        if stats is not None:
+            stats.extend(st)
+        if warm is not None:
+            for i, q in enumerate(g):
+                warm[q] = u[i].clone()
         res = torch.empty_like(far)
         y = prob.y[g].contiguous()
         l2 = ls_residual(far, y, res)
@@ -130,15 +114,20 @@ class FistaState:
 
 def fista(prob: Problem, f0: torch.Tensor, iters: int, gamma0: float, tau: float, tv_iters: int = 20,
           subset: int | None = None, seed: int = 0, batched: bool = True, state: FistaState | None = None,
-          checkpoint: str | None = None, checkpoint_every: int = 0, f_true: torch.Tensor | None = None):
-    """Runs `iters` FISTA iterations (Alg. 1); returns the final state (history: (k, loss, rel_err, s))."""
+          checkpoint: str | None = None, checkpoint_every: int = 0, f_true: torch.Tensor | None = None,
+          warm_start: bool = False, solver_stats: list | None = None):
+    """Runs `iters` FISTA iterations (Alg. 1); returns the final state (history: (k, loss, rel_err, s)).
+
+    warm_start: start each view's forward solve from its field of the last iteration that used it.
+    solver_stats: list that receives the forward solves' per-view statistics."""
     rng = np.random.default_rng(seed)
     Q = prob.kvec.shape[0]
     st = state or FistaState(f0.clone(), f0.clone(), f0.clone())
+    warm = {} if warm_start else None
     t0 = time.perf_counter()
     for _ in range(iters):
         views = None if not subset else sorted(rng.choice(Q, size=subset, replace=False).tolist())
-        loss, d = data_grad(prob, st.v, views, batched)
+        loss, d = data_grad(prob, st.v, views, batched, warm=warm, stats=solver_stats)
         if views is not None:
             d = d * (Q / len(views))
         gamma = gamma0 / math.sqrt(st.k)
