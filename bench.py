@@ -581,15 +581,20 @@ def run_fista_mode(args):
     gamma0 = 0.5 * float(f_true.abs().max()) / float(d0.abs().max())
     out = {"mode": "fista", "workload": "128^3, 60 views NA 0.8, 20 ellipsoids dn <= 0.1, 1% noise, TV + positivity",
            "iterations": args.fista_iters, "gamma0": gamma0, "tau": args.tau}
-    for name, batched in (("batched", True), ("one_view_at_a_time", False)):
+    for name, batched, warm in (("batched", True, False), ("batched_warm_start", True, True),
+                                ("one_view_at_a_time", False, False)):
         torch.cuda.synchronize()
+        solver = []
         t0 = _t.perf_counter()
         st = recon.fista(prob, f0, args.fista_iters, gamma0=gamma0, tau=args.tau, tv_iters=10, batched=batched,
-                         f_true=f_true)
+                         f_true=f_true, warm_start=warm, solver_stats=solver)
         torch.cuda.synchronize()
         out[name] = {"seconds": round(_t.perf_counter() - t0, 2), "final_rel_error": st.history[-1][2],
-                     "final_loss": st.history[-1][1]}
+                     "final_loss": st.history[-1][1],
+                     "mean_forward_iterations": round(float(np.mean([s["iterations"] for s in solver])), 3)}
     out["speedup_batched"] = round(out["one_view_at_a_time"]["seconds"] / out["batched"]["seconds"], 3)
+    out["speedup_batched_warm_start"] = round(out["one_view_at_a_time"]["seconds"]
+                                              / out["batched_warm_start"]["seconds"], 3)
     plan.close()
     print(json.dumps(out))
 
