@@ -857,8 +857,7 @@ int ls_plane_waves(ls_plan* P, int n_views, const double* kvec, ls_c64* const* u
   rc = engine_upload_ptrs(P, 0, (const void* const*)u_in, n_views, st);
   if (rc) return rc;
   PlaneWaveParams a{P->nx, P->ny, P->nz, P->h, P->eng.kvec_d, (float2* const*)engine_ptr_table(P, 0)};
-  launch_plane_waves(a, n_views, st);
-  LS_CUDA_TRY(cudaGetLastError());
+  LS_CUDA_TRY(launch_plane_waves(a, n_views, st));
   return LS_OK;
 }
 

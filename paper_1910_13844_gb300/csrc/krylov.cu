@@ -186,23 +186,38 @@ __global__ void k_count(const SlotDev* slots, int nslots, int* out) {
 
 // ------------------------------------------------------------------ element-wise kernels
 
-// u_in,q(x) = exp(i k_q . x) at voxel centres; phase reduced mod 2 pi in float64 (Fig. 1).
+// u_in,q(x) = exp(i k_q . x) at voxel centres (Fig. 1) is separable: exp(i kx x) exp(i ky y) exp(i kz z).
+// The three 1-D factors are evaluated per view with the phase reduced mod 2 pi in float64
+// (tables [view][nx + ny + nz]); the volume is their complex64 product.
+__global__ void k_plane_tables(PlaneWaveParams a) {
+  const int q = blockIdx.y;
+  const int m = a.nx + a.ny + a.nz;
+  const double twopi = 6.283185307179586476925286766559;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+    int axis = 0, idx = j, n = a.nx;
+    if (j >= a.nx + a.ny) { axis = 2; idx = j - a.nx - a.ny; n = a.nz; }
+    else if (j >= a.nx) { axis = 1; idx = j - a.nx; n = a.ny; }
+    double ph = a.k[3 * q + axis] * (a.h * (idx - n / 2 + 1));
+    ph -= twopi * rint(ph / twopi);
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    a.tables[(size_t)q * m + j] = make_float2((float)cs, (float)sn);
+  }
+}
+
 __global__ void k_plane_waves(PlaneWaveParams a) {
   const int q = blockIdx.y;
-  const double kx = a.k[3 * q], ky = a.k[3 * q + 1], kz = a.k[3 * q + 2];
+  const float2* ex = a.tables + (size_t)q * (a.nx + a.ny + a.nz);
+  const float2* ey = ex + a.nx;
+  const float2* ez = ey + a.ny;
   float2* out = a.out[q];
-  const size_t n = (size_t)a.nx * a.ny * a.nz;
-  const double twopi = 6.283185307179586476925286766559;
+  const size_t plane = (size_t)a.nx * a.ny;
+  const size_t n = plane * a.nz;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int ix = (int)(i % a.nx);
     const int iy = (int)((i / a.nx) % a.ny);
-    const int iz = (int)(i / ((size_t)a.nx * a.ny));
-    const double x = a.h * (ix - a.nx / 2 + 1), y = a.h * (iy - a.ny / 2 + 1), z = a.h * (iz - a.nz / 2 + 1);
-    double ph = kx * x + ky * y + kz * z;
-    ph -= twopi * rint(ph / twopi);
-    float sn, cs;
-    sincosf((float)ph, &sn, &cs);
-    out[i] = make_float2(cs, sn);
+    const int iz = (int)(i / plane);
+    out[i] = cmul(__ldg(ez + iz), cmul(__ldg(ey + iy), __ldg(ex + ix)));
   }
 }
 
@@ -295,11 +310,19 @@ void launch_scalar(const ScalarParams& a, int nslots, cudaStream_t st) {
 void launch_count(const SlotDev* slots, int nslots, int* out, cudaStream_t st) {
   k_count<<<1, 256, 0, st>>>(slots, nslots, out);
 }
-void launch_plane_waves(const PlaneWaveParams& a, int nviews, cudaStream_t st) {
+cudaError_t launch_plane_waves(const PlaneWaveParams& a0, int nviews, cudaStream_t st) {
+  PlaneWaveParams a = a0;
+  const int m = a.nx + a.ny + a.nz;
+  cudaError_t e = cudaMallocAsync((void**)&a.tables, (size_t)nviews * m * sizeof(float2), st);
+  if (e != cudaSuccess) return e;
+  k_plane_tables<<<dim3((m + 127) / 128, nviews), 128, 0, st>>>(a);
   const size_t n = (size_t)a.nx * a.ny * a.nz;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 1216) blocks = 1216;
   k_plane_waves<<<dim3(blocks, nviews), 256, 0, st>>>(a);
+  e = cudaGetLastError();
+  cudaError_t f = cudaFreeAsync(a.tables, st);
+  return e != cudaSuccess ? e : f;
 }
 void launch_potential(const float* dn, size_t count, double eta_b, double kb, float* f, cudaStream_t st) {
   int blocks = (int)((count + 255) / 256);

@@ -29,6 +29,7 @@ struct PlaneWaveParams {
   double h;
   const double* k;          // device, 3 per view
   float2* const* out;       // device array of device pointers
+  float2* tables = nullptr; // per-view 1-D phase factors (allocated by the launcher)
 };
 
 struct FarParams {
@@ -67,7 +68,7 @@ struct ResidualParams {
 void launch_update(const UpdParams& a, int nblocks, int nslots, cudaStream_t st);
 void launch_scalar(const ScalarParams& a, int nslots, cudaStream_t st);
 void launch_count(const SlotDev* slots, int nslots, int* out, cudaStream_t st);
-void launch_plane_waves(const PlaneWaveParams& a, int nviews, cudaStream_t st);
+cudaError_t launch_plane_waves(const PlaneWaveParams& a, int nviews, cudaStream_t st);
 void launch_potential(const float* dn, size_t count, double eta_b, double kb, float* f, cudaStream_t st);
 void launch_far_reduce(const FarParams& a, int nslots, cudaStream_t st);
 void launch_far_adjoint_mul(const FarParams& a, int nslots, cudaStream_t st);
