@@ -8,6 +8,10 @@
 
 #include <math.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 namespace lsgpu {
 
 // -------------------------------------------------------------- ghat_t
@@ -20,15 +24,24 @@ __device__ __forceinline__ double sinc_d(double x) {
 // frequency w.  Written as
 //   ghat_t(w) = R [sin(R d/2) sinc(R d/2) + i sinc(R d) - i e^{i k R} sinc(R w)] / (w + k),  d = w - k,
 // which is the same function as eq. GreenL but has no 0/0 at w = k: there it
-// gives eq. GreenL2, i (R/(2k) - e^{ikR} sin(kR)/(2k^2)).
-__device__ double2 ghat_t(double w, double k, double R) {
-  const double d = w - k;
-  const double a = 0.5 * R * d;
-  double re = R * sin(a) * sinc_d(a);
-  double im = R * sinc_d(R * d);
+// gives eq. GreenL2, i (R/(2k) - e^{ikR} sin(kR)/(2k^2)).  With a = R d / 2 the first two terms
+// need only sin a and cos a: sin(a) sinc(a) = sin(a)^2 / a and sinc(2a) = sinc(a) cos(a).
+// skr, ckr = sin(kR), cos(kR).
+__device__ double2 ghat_t(double w, double k, double R, double skr, double ckr) {
+  const double a = 0.5 * R * (w - k);
+  double sa, ca, sinc_a;
+  if (fabs(a) < 1e-4) {
+    const double a2 = a * a;
+    sinc_a = 1.0 - a2 / 6.0 + a2 * a2 / 120.0;
+    sa = a * sinc_a;
+    ca = 1.0 - a2 / 2.0 + a2 * a2 / 24.0;
+  } else {
+    sincos(a, &sa, &ca);
+    sinc_a = sa / a;
+  }
+  double re = R * sa * sinc_a;
+  double im = R * sinc_a * ca;
   const double s = sinc_d(R * w);
-  double skr, ckr;
-  sincos(k * R, &skr, &ckr);
   re += R * s * skr;
   im -= R * s * ckr;
   const double inv = 1.0 / (w + k);
@@ -41,32 +54,49 @@ __device__ __forceinline__ int centred(int q, int M) { return q > M / 2 ? q - M 
 __global__ void k_sample_sublattice(GreenBuildParams a, int sz, int sy, int sx, double2* S) {
   const size_t total = (size_t)a.Mx * a.My * a.Mz;
   const int half = a.p / 2;
+  double skr, ckr;
+  sincos(a.kb * a.R, &skr, &ckr);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const int qx = (int)(i % a.Mx), qy = (int)((i / a.Mx) % a.My), qz = (int)(i / ((size_t)a.Mx * a.My));
     const double wx = a.dx * (half * centred(qx, a.Mx) - sx);
     const double wy = a.dy * (half * centred(qy, a.My) - sy);
     const double wz = a.dz * (half * centred(qz, a.Mz) - sz);
-    S[i] = ghat_t(sqrt(wx * wx + wy * wy + wz * wz), a.kb, a.R);
+    S[i] = ghat_t(sqrt(wx * wx + wy * wy + wz * wz), a.kb, a.R, skr, ckr);
   }
 }
 
-// K[k] += scale * T[k] * exp(-2 pi i (c(kx) sx/(nx p) + c(ky) sy/(ny p) + c(kz) sz/(nz p)))
-__global__ void k_prop1_accumulate(GreenBuildParams a, int sz, int sy, int sx, const double2* T, double2* K,
-                                   double scale) {
-  const size_t total = (size_t)a.Mx * a.My * a.Mz;
-  const int np_x = a.Mx / 2 * a.p, np_y = a.My / 2 * a.p, np_z = a.Mz / 2 * a.p;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int kx = (int)(i % a.Mx), ky = (int)((i / a.Mx) % a.My), kz = (int)(i / ((size_t)a.Mx * a.My));
-    // phase as a fraction of a turn, reduced exactly with integer arithmetic per axis
-    const double turns = (double)((long long)centred(kx, a.Mx) * sx % np_x) / np_x +
-                         (double)((long long)centred(ky, a.My) * sy % np_y) / np_y +
-                         (double)((long long)centred(kz, a.Mz) * sz % np_z) / np_z;
+// Phase factors of Prop. 1's sub-lattice shift s, one table per axis:
+// ph[k] = exp(-2 pi i c(k) s / (n p)) for k < M on each axis (x, then y, then z), the turn count
+// reduced exactly with integer arithmetic.
+__global__ void k_prop1_phases(GreenBuildParams a, int sz, int sy, int sx, double2* ph) {
+  const int m = a.Mx + a.My + a.Mz;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+    int M = a.Mx, k = j, s = sx;
+    if (j >= a.Mx + a.My) { M = a.Mz; k = j - a.Mx - a.My; s = sz; }
+    else if (j >= a.Mx) { M = a.My; k = j - a.Mx; s = sy; }
+    const int np = M / 2 * a.p;
+    const double turns = (double)((long long)centred(k, M) * s % np) / np;
     double sn, cs;
     sincospi(-2.0 * turns, &sn, &cs);
-    const double2 t = T[i];
+    ph[j] = make_double2(cs, sn);
+  }
+}
+
+// K[k] += scale * T[k] * ph_x[kx] ph_y[ky] ph_z[kz]
+//   (= exp(-2 pi i (c(kx) sx/(nx p) + c(ky) sy/(ny p) + c(kz) sz/(nz p))), Prop. 1)
+__global__ void k_prop1_accumulate(GreenBuildParams a, const double2* ph, const double2* T, double2* K,
+                                   double scale) {
+  const size_t total = (size_t)a.Mx * a.My * a.Mz;
+  const double2* px = ph;
+  const double2* py = ph + a.Mx;
+  const double2* pz = ph + a.Mx + a.My;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % a.Mx), ky = (int)((i / a.Mx) % a.My), kz = (int)(i / ((size_t)a.Mx * a.My));
+    const double2 e = zmul(pz[kz], zmul(py[ky], px[kx]));
+    const double2 t = zmul(T[i], e);
     double2 acc = K[i];
-    acc.x += scale * (t.x * cs - t.y * sn);
-    acc.y += scale * (t.x * sn + t.y * cs);
+    acc.x += scale * t.x;
+    acc.y += scale * t.y;
     K[i] = acc;
   }
 }
@@ -159,7 +189,7 @@ __device__ __forceinline__ void zdft(double2* v, int r, int dir) {
 }
 
 __global__ void k_fft64(double2* data, int L, size_t elem_stride, int ninner, size_t inner_stride,
-                        size_t outer_stride, int dir) {
+                        size_t outer_stride, int dir, const double2* __restrict__ tw) {
   extern __shared__ double2 zb[];
   double2* b0 = zb;
   double2* b1 = zb + L;
@@ -179,9 +209,10 @@ __global__ void k_fft64(double2* data, int L, size_t elem_stride, int ninner, si
       for (int q = 0; q < r; ++q) {
         v[q] = src[j + q * m];
         if (q > 0) {
-          double sn, cs;
-          sincospi((double)dir * 2.0 * (double)(k * q) / (double)(Ns * r), &sn, &cs);
-          v[q] = zmul(v[q], make_double2(cs, sn));
+          // exp(dir 2 pi i k q / (Ns r)) = tw[k q L / (Ns r)] (conjugated for dir = +1)
+          double2 w = tw[(size_t)k * q * (L / (Ns * r)) % L];
+          if (dir > 0) w.y = -w.y;
+          v[q] = zmul(v[q], w);
         }
       }
       zdft(v, r, dir);
@@ -196,21 +227,54 @@ __global__ void k_fft64(double2* data, int L, size_t elem_stride, int ninner, si
   for (int i = threadIdx.x; i < L; i += blockDim.x) data[base + (size_t)i * elem_stride] = src[i];
 }
 
+// exp(-2 pi i j / L), j < L, in float64
+__global__ void k_twiddle64(int L, double2* w) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < L; j += gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * (double)j / (double)L, &sn, &cs);
+    w[j] = make_double2(cs, sn);
+  }
+}
+
+// Twiddle table of length L on the current device, built on first use and kept for the process
+// (a few KB per length); the first build is synchronous so every stream may read it.
+static const double2* twiddle64(int L, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, double2*> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({dev, L});
+  if (it != cache.end()) return it->second;
+  double2* w = nullptr;
+  if (cudaMalloc((void**)&w, (size_t)L * sizeof(double2)) != cudaSuccess) return nullptr;
+  k_twiddle64<<<(L + 127) / 128, 128, 0, st>>>(L, w);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { cudaFree(w); return nullptr; }
+  cache[{dev, L}] = w;
+  return w;
+}
+
+static void fft64_pass(double2* d, int L, size_t pencils, size_t elem_stride, int ninner, size_t inner_stride,
+                       size_t outer_stride, int dir, cudaStream_t st) {
+  const double2* tw = twiddle64(L, st);
+  if (!tw) return;   // the allocation error is left for the caller's cudaGetLastError
+  k_fft64<<<(unsigned)pencils, 128, 2 * L * sizeof(double2), st>>>(d, L, elem_stride, ninner, inner_stride,
+                                                                    outer_stride, dir, tw);
+}
+
 // 3-D (or 2-D when Mz == 1) in-place float64 FFT of a [Mz][My][Mx] array.
 void fft64_3d(double2* d, int Mx, int My, int Mz, int dir, cudaStream_t st) {
-  const int thr = 128;
   // x: pencils are rows
-  k_fft64<<<(unsigned)((size_t)My * Mz), thr, 2 * Mx * sizeof(double2), st>>>(d, Mx, 1, 1, 0, Mx, dir);
+  fft64_pass(d, Mx, (size_t)My * Mz, 1, 1, 0, Mx, dir, st);
   // y: pencils (z, x)
-  k_fft64<<<(unsigned)((size_t)Mx * Mz), thr, 2 * My * sizeof(double2), st>>>(d, My, Mx, Mx, 1, (size_t)Mx * My, dir);
-  if (Mz > 1)
-    k_fft64<<<(unsigned)((size_t)Mx * My), thr, 2 * Mz * sizeof(double2), st>>>(d, Mz, (size_t)Mx * My, Mx * My, 1, 0, dir);
+  fft64_pass(d, My, (size_t)Mx * Mz, Mx, Mx, 1, (size_t)Mx * My, dir, st);
+  if (Mz > 1) fft64_pass(d, Mz, (size_t)Mx * My, (size_t)Mx * My, Mx * My, 1, 0, dir, st);
 }
 
 // 2-D in-place float64 FFT of `planes` stacked [My][Mx] arrays.
 void fft64_2d_planes(double2* d, int Mx, int My, int planes, int dir, cudaStream_t st) {
-  k_fft64<<<(unsigned)((size_t)My * planes), 128, 2 * Mx * sizeof(double2), st>>>(d, Mx, 1, 1, 0, Mx, dir);
-  k_fft64<<<(unsigned)((size_t)Mx * planes), 128, 2 * My * sizeof(double2), st>>>(d, My, Mx, Mx, 1, (size_t)Mx * My, dir);
+  fft64_pass(d, Mx, (size_t)My * planes, 1, 1, 0, Mx, dir, st);
+  fft64_pass(d, My, (size_t)Mx * planes, Mx, Mx, 1, (size_t)Mx * My, dir, st);
 }
 
 static int grid_for(size_t n) {
@@ -226,13 +290,19 @@ cudaError_t build_green_octant(const GreenBuildParams& a, double2* S, double2* K
   const int nx = a.Mx / 2, ny = a.My / 2, nz = a.Mz / 2;
   // (np)^{-3} = (8/p^3) * 1/((2nx)(2ny)(2nz)) folds F^{-1}_{2n}'s normalisation and Prop. 1's factor
   const double scale = 1.0 / ((double)a.p * a.p * a.p * (double)nx * ny * nz);
+  double2* ph = nullptr;
+  e = cudaMallocAsync((void**)&ph, (size_t)(a.Mx + a.My + a.Mz) * sizeof(double2), st);
+  if (e != cudaSuccess) return e;
   for (int sz = 0; sz < half; ++sz)
     for (int sy = 0; sy < half; ++sy)
       for (int sx = 0; sx < half; ++sx) {
         k_sample_sublattice<<<grid_for(total), 256, 0, st>>>(a, sz, sy, sx, S);
         fft64_3d(S, a.Mx, a.My, a.Mz, +1, st);
-        k_prop1_accumulate<<<grid_for(total), 256, 0, st>>>(a, sz, sy, sx, S, K, scale);
+        k_prop1_phases<<<(a.Mx + a.My + a.Mz + 127) / 128, 128, 0, st>>>(a, sz, sy, sx, ph);
+        k_prop1_accumulate<<<grid_for(total), 256, 0, st>>>(a, ph, S, K, scale);
       }
+  e = cudaFreeAsync(ph, st);
+  if (e != cudaSuccess) return e;
   k_zero_nyquist<<<grid_for(total), 256, 0, st>>>(a, K);
   fft64_3d(K, a.Mx, a.My, a.Mz, -1, st);
   const size_t oct_n = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
@@ -250,9 +320,7 @@ cudaError_t build_far_kernels(const FarKernelParams& a, double2* K2, float2* out
   const size_t total = (size_t)4 * a.nx * a.ny * a.nz;
   k_far_kernel<<<grid_for(total), 256, 0, st>>>(a, K2);
   // 2-D FFT of every slice: x then y pencils, z stays
-  const int Mx = 2 * a.nx, My = 2 * a.ny;
-  k_fft64<<<(unsigned)((size_t)My * a.nz), 128, 2 * Mx * sizeof(double2), st>>>(K2, Mx, 1, 1, 0, Mx, -1);
-  k_fft64<<<(unsigned)((size_t)Mx * a.nz), 128, 2 * My * sizeof(double2), st>>>(K2, My, Mx, Mx, 1, (size_t)Mx * My, -1);
+  fft64_2d_planes(K2, 2 * a.nx, 2 * a.ny, a.nz, -1, st);
   k_to_c64<<<grid_for(total), 256, 0, st>>>(K2, out, total, 1.0 / (4.0 * a.nx * a.ny));
   return cudaGetLastError();
 }
