@@ -199,6 +199,16 @@ int ls_apply_pupil(ls_plan* plan, int n_views, const ls_c64* const* in, ls_c64* 
 int ls_prox_tv(const ls_grid* grid, const float* z, float* x, double lam, int iters, float* work,
                void* cuda_stream);
 
+/* x = argmin_{x >= 0} 0.5 ||x - z||^2 + lam sum_v ||H x (v)||_{S1}: the prox step of Alg. 1 with the
+ * Hessian Schatten-norm regulariser (Sec. 4.2), H the discrete Hessian (second differences D_aa =
+ * -D_a^T D_a with a Neumann boundary, mixed D_ab = D_b D_a of forward differences), ||.||_{S1} the
+ * nuclear norm of each voxel's symmetric 3 x 3 Hessian; evaluated by `iters` FGP iterations on the
+ * dual (spectral-norm ball per voxel, step 1/(144 lam)).  z, x: device float [nz][ny][nx] that must
+ * not overlap when lam > 0; work: device scratch of 12*nx*ny*nz floats, or NULL to allocate it on the
+ * stream.  lam <= 0 gives max(z, 0).  Asynchronous on cuda_stream. */
+int ls_prox_hs(const ls_grid* grid, const float* z, float* x, double lam, int iters, float* work,
+               void* cuda_stream);
+
 /* Incident fields from their measurement on the detector plane (Sec. 3.4): for every plane z of
  * the volume, u_in(., z) = p_z * y_in with p_hat_z(w) = exp(-i (x_gamma - z) sqrt(k_b^2 - |w|^2))
  * (eq. propUin; evanescent components dropped), computed as a periodic convolution on the

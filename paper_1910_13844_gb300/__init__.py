@@ -28,7 +28,7 @@ __all__ = [
     "ls_farfield_adjoint", "ls_residual", "ls_gradient", "ls_server_create", "ls_submit", "ls_poll",
     "ls_server_destroy", "ls_status_string", "ls_last_error", "ls_workspace_bytes", "ls_profile", "library_path",
     "ls_matvec_noalloc", "ls_matvec_batch", "Server", "ls_set_pupil", "ls_apply_pupil", "ls_incident_field",
-    "ls_forward_warm", "ls_prox_tv",
+    "ls_forward_warm", "ls_prox_tv", "ls_prox_hs",
 ]
 
 _SOFT = (LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN, LS_TIMEOUT, LS_PENDING)
@@ -218,6 +218,16 @@ def ls_prox_tv(z, x, lam: float, iters: int = 20, work=None, stream=None) -> int
     g = ls_grid(nx, ny, nz)
     return _check(_lib.ls_prox_tv(C.byref(g), _ptr(z), _ptr(x), float(lam), int(iters),
                                   _ptr(work) if work is not None else None, _stream(stream)), "ls_prox_tv")
+
+
+def ls_prox_hs(z, x, lam: float, iters: int = 20, work=None, stream=None) -> int:
+    """x = prox of lam * (Hessian Schatten-1 norm) + i_{>=0} at z (float32 CUDA (nz, ny, nx)), FGP."""
+    if z.dim() != 3 or z.shape != x.shape:
+        raise ValueError("z and x must be (nz, ny, nx) tensors of the same shape")
+    nz, ny, nx = z.shape
+    g = ls_grid(nx, ny, nz)
+    return _check(_lib.ls_prox_hs(C.byref(g), _ptr(z), _ptr(x), float(lam), int(iters),
+                                  _ptr(work) if work is not None else None, _stream(stream)), "ls_prox_hs")
 
 
 def ls_farfield(plan: int, f, u, far, stream=None) -> int:

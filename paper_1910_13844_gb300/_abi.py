@@ -80,6 +80,7 @@ SIGNATURES = {
     "ls_forward": (C.c_int, [_P, _P, C.c_int, _PP, _PP, _PP, C.POINTER(ls_stats), _P]),
     "ls_forward_warm": (C.c_int, [_P, _P, C.c_int, _PP, _PP, _PP, _PP, C.POINTER(ls_stats), _P]),
     "ls_prox_tv": (C.c_int, [C.POINTER(ls_grid), _P, _P, C.c_double, C.c_int, _P, _P]),
+    "ls_prox_hs": (C.c_int, [C.POINTER(ls_grid), _P, _P, C.c_double, C.c_int, _P, _P]),
     "ls_farfield": (C.c_int, [_P, _P, C.c_int, _PP, _PP, _P]),
     "ls_farfield_adjoint": (C.c_int, [_P, C.c_int, _PP, _PP, _P]),
     "ls_residual": (C.c_int, [C.c_int, C.c_size_t, _PP, _PP, _PP, C.POINTER(C.c_double), _P]),

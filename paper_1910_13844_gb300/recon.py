@@ -24,7 +24,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import ls_forward, ls_forward_warm, ls_gradient, ls_plane_waves, ls_prox_tv, ls_residual
+from . import ls_forward, ls_forward_warm, ls_gradient, ls_plane_waves, ls_prox_hs, ls_prox_tv, ls_residual
 
 
 # ------------------------------------------------------------------ TV prox (FGP)
@@ -33,6 +33,16 @@ def prox_tv_nonneg(z: torch.Tensor, lam: float, iters: int = 20) -> torch.Tensor
     x = torch.empty_like(z)
     ls_prox_tv(z.contiguous(), x, lam, iters)
     return x
+
+
+def prox_hs_nonneg(z: torch.Tensor, lam: float, iters: int = 20) -> torch.Tensor:
+    """argmin_x 0.5 ||x - z||^2 + lam sum_v ||H x (v)||_{S1} + i_{>=0}(x) (Hessian Schatten norm), FGP."""
+    x = torch.empty_like(z)
+    ls_prox_hs(z.contiguous(), x, lam, iters)
+    return x
+
+
+PROX = {"tv": prox_tv_nonneg, "hs": prox_hs_nonneg}
 
 
 # ------------------------------------------------------------------ data term
@@ -115,11 +125,13 @@ class FistaState:
 def fista(prob: Problem, f0: torch.Tensor, iters: int, gamma0: float, tau: float, tv_iters: int = 20,
           subset: int | None = None, seed: int = 0, batched: bool = True, state: FistaState | None = None,
           checkpoint: str | None = None, checkpoint_every: int = 0, f_true: torch.Tensor | None = None,
-          warm_start: bool = False, solver_stats: list | None = None):
+          warm_start: bool = False, solver_stats: list | None = None, reg: str = "tv"):
     """Runs `iters` FISTA iterations (Alg. 1); returns the final state (history: (k, loss, rel_err, s)).
 
     warm_start: start each view's forward solve from its field of the last iteration that used it.
-    solver_stats: list that receives the forward solves' per-view statistics."""
+    solver_stats: list that receives the forward solves' per-view statistics.
+    reg: "tv" (total variation) or "hs" (Hessian Schatten 1-norm), both with positivity."""
+    prox = PROX[reg]
     rng = np.random.default_rng(seed)
     Q = prob.kvec.shape[0]
     st = state or FistaState(f0.clone(), f0.clone(), f0.clone())
@@ -131,7 +143,7 @@ def fista(prob: Problem, f0: torch.Tensor, iters: int, gamma0: float, tau: float
         if views is not None:
             d = d * (Q / len(views))
         gamma = gamma0 / math.sqrt(st.k)
-        f_new = prox_tv_nonneg(st.v - gamma * d, gamma * tau, tv_iters)
+        f_new = prox(st.v - gamma * d, gamma * tau, tv_iters)
         alpha_next = (1.0 + math.sqrt(1.0 + 4.0 * st.alpha * st.alpha)) / 2.0
         st.v = f_new + ((st.alpha - 1.0) / alpha_next) * (f_new - st.f)
         st.f_prev, st.f = st.f, f_new

@@ -108,3 +108,51 @@ def test_fista_with_warm_starts_matches_cold_starts():
     assert rel(b.f.cpu().numpy(), a.f.cpu().numpy()) < 1e-4
     assert sum(s["iterations"] for s in warm_stats) < sum(s["iterations"] for s in cold_stats)
     plan.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape,iters", [((12, 10, 9), 30), ((24, 20, 16), 20), ((64, 64, 64), 20), ((9, 1, 1), 40)])
+def test_prox_hs_matches_oracle(shape, iters):
+    from oracle import hessian as hs
+
+    torch, ls = torch_and_lib()
+    rng = np.random.default_rng(12)
+    z = 0.5 + rng.standard_normal(shape)
+    lam = 0.02
+    zd = to_dev(torch, z, torch.float32)
+    x = torch.empty_like(zd)
+    ls.ls_prox_hs(zd, x, lam, iters)
+    torch.cuda.synchronize()
+    ref = hs.prox_hs_nonneg(zd.cpu().numpy().astype(np.float64), lam, iters)
+    assert rel(x.cpu().numpy(), ref) < 1e-4
+    assert float(x.min()) >= 0.0
+    y = torch.empty_like(zd)
+    ls.ls_prox_hs(zd, y, 0.0, 5)
+    torch.cuda.synchronize()
+    assert torch.equal(y, zd.clamp_min(0.0))
+    with pytest.raises(ls.LsError):
+        ls.ls_prox_hs(zd, zd, lam, 5)
+
+
+@pytest.mark.gpu
+def test_fista_with_the_hessian_schatten_regulariser_reduces_the_error():
+    torch, ls = torch_and_lib()
+    from paper_1910_13844_gb300 import recon
+
+    shape = (32, 32, 32)
+    f_true = to_dev(torch, potential(ph.random_ellipsoids(shape, count=5, rmin=4, rmax=10, dn_max=0.05)),
+                    torch.float32)
+    kvec = ph.cone_directions(8, 0.8) * KB
+    plan = ls.Plan(shape, KB, H, tol=1e-6)
+    uin = plan.plane_waves(kvec)
+    _, y, code, _ = plan.forward(f_true, uin, want_fields=False)
+    prob = recon.Problem(plan, kvec, y)
+    f0 = torch.zeros_like(f_true)
+    _, d0 = recon.data_grad(prob, f0)
+    kw = dict(gamma0=0.5 * float(f_true.abs().max()) / float(d0.abs().max()), tau=1e-5, tv_iters=10,
+              f_true=f_true)
+    st = recon.fista(prob, f0, 10, reg="hs", **kw)
+    errs = [h[2] for h in st.history]
+    assert errs[-1] < errs[0] and errs[-1] < 0.9      # squared relative error from 1.0 at f = 0
+    assert float(st.f.min()) >= 0.0
+    plan.close()
