@@ -707,6 +707,10 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
 }
 
 // ------------------------------------------------------------------------- IX
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
+
 template <int L>
 __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
   using G = Geo<L>;
@@ -719,6 +723,14 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
   const int nx = L / 2;
   const int row = blockIdx.x * G::PC + p;
   const bool valid = row < a.rows;
+  // the epilogue's operands are read after both transforms: ask L2 for their lines now (one
+  // 128-byte line per thread and vector; a row holds nx/16 lines)
+  if (valid && a.mode != IX_STORE) {
+    constexpr int lines = (L / 2) / 16;
+    const size_t voff0 = (size_t)slot * a.vstride + (size_t)row * nx;
+    if (t < lines) prefetch_l2(a.in0 + voff0 + 16 * t);
+    else if (t < 2 * lines && (a.mode == IX_BICG_V || a.mode == IX_RESID)) prefetch_l2(a.in1 + voff0 + 16 * (t - lines));
+  }
   float2 v[R1];
 #pragma unroll
   for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
