@@ -265,7 +265,10 @@ struct ls_server {
     cudaMemcpyAsync(e.kvec_d + 3 * (size_t)r->s0, r->kvec.data(), 3 * r->n * sizeof(double), cudaMemcpyHostToDevice, st);
     PlaneWaveParams a{P->nx, P->ny, P->nz, P->h, e.kvec_d + 3 * (size_t)r->s0,
                       (float2* const*)(engine_ptr_table(P, 0) + r->s0)};
-    launch_plane_waves(a, r->n, st);
+    if (launch_plane_waves(a, r->n, st) != cudaSuccess) {
+      fail(r, LS_ECUDA);
+      return;
+    }
     cudaMemcpyAsync(e.vptr(V_X, r->s0), e.vptr(V_B, r->s0), (size_t)r->n * e.N * sizeof(float2),
                     cudaMemcpyDeviceToDevice, st);
     for (int q = 0; q < r->n; ++q) slot_defaults(P, e.slots_h[r->s0 + q], r->req.f, 0);
