@@ -104,6 +104,10 @@ __device__ __forceinline__ bool slot_runs(const SlotSel& s, int slot) {
 __device__ __forceinline__ void count_run(const SlotSel& s) {
   if (s.runs && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(s.runs, 1ull);
 }
+// the same for kernels whose first block of a slot is `first`
+__device__ __forceinline__ void count_run_if(const SlotSel& s, bool first) {
+  if (s.runs && first && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(s.runs, 1ull);
+}
 // Ordered list of the slots of this launch that run (every CTA builds the same list).
 // Block size must be a multiple of 32.  Returns the number of active slots.
 __device__ __forceinline__ int build_active(const SlotSel& s, int* list, int* wsum) {
@@ -214,12 +218,14 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_fx(FxParams a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
-  const int slot = blockIdx.y;
+  // slots vary fastest in launch order, so the CTAs of all views that share a row block (and the
+  // potential's rows, common to the views of one sample) run together and f is read from L2
+  const int slot = blockIdx.x;
   if (!slot_runs(a.sel, slot)) return;
-  count_run(a.sel);
+  count_run_if(a.sel, blockIdx.y == 0);
   const int t = threadIdx.x, p = threadIdx.y;
   const int nx = L / 2;
-  const int row = blockIdx.x * G::PC + p;
+  const int row = blockIdx.y * G::PC + p;
   const bool valid = row < a.rows;
   const size_t voff = (size_t)slot * a.vstride + (size_t)row * nx;
   const float* f = slot_f(a.sel, slot);
@@ -815,7 +821,7 @@ template <int L>
 struct PassImpl {
   using G = Geo<L>;
   static void fx(const FxParams& a, int nslots, cudaStream_t st) {
-    dim3 blk(G::T, G::PC), grd((a.rows + G::PC - 1) / G::PC, nslots);
+    dim3 blk(G::T, G::PC), grd(nslots, (a.rows + G::PC - 1) / G::PC);
     k_fx<L><<<grd, blk, G::smem_contig, st>>>(a);
   }
   static void ix(const IxParams& a, int nslots, cudaStream_t st) {
