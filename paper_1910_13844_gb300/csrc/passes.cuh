@@ -513,6 +513,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
     if (global_ns() - t0 > 1000000000ull) return false;
   return true;
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+// mbar_wait that also gives up as soon as another thread of the CTA has set *abort; a wait that
+// runs out sets *abort itself.
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (global_ns() - t0 > 1000000000ull) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
                                             int c3) {
   asm volatile(
@@ -541,8 +558,8 @@ struct ZW {
   static constexpr bool ok = (32 % T) == 0;
   static constexpr int CPW = ok ? 32 / T : 1;   // whole columns per warp (lane = t * CPW + column)
   static constexpr int P = 16;                  // columns per CTA: one 128-byte TMA row
-  static constexpr int NW = P / CPW;
-  static constexpr int NT = 32 * NW;
+  static constexpr int NW = P / CPW;             // compute warps
+  static constexpr int NT = 32 * NW + 32;        // + one producer warp (TMA loads and stores)
   static constexpr int NZ = L / 2;
   static constexpr int MINB = NT >= 512 ? 1 : NT >= 256 ? 2 : 512 / NT;
   // exchange pitch per column (in float2) congruent to 16/CPW mod 16: the CPW columns of a half-warp
@@ -557,7 +574,7 @@ struct ZW {
   static constexpr size_t off_twa = off_x + (size_t)P * XP * sizeof(float2);
   static constexpr size_t off_twb = off_twa + (size_t)R2 * TWA * sizeof(float2);
   static constexpr size_t off_bar = off_twb + (size_t)R1 * TWB * sizeof(float2);
-  static constexpr size_t smem = off_bar + 2 * sizeof(uint64_t) + 1024;      // + room to align the base to 1024
+  static constexpr size_t smem = off_bar + 4 * sizeof(uint64_t) + 1024;      // + room to align the base to 1024
 };
 
 // Byte offset of element (z, c) of a [NZ][16] complex64 tile written by TMA with the 128-byte swizzle
@@ -579,7 +596,7 @@ __device__ __forceinline__ void green_mul(float2 (&u)[R2], const float2* gc, int
 template <int L>
 __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_constant__ ZParams a) {
   using W = ZW<L>;
-  constexpr int R1 = W::R1, R2 = W::R2, P = W::P, NZ = W::NZ, CPW = W::CPW, T = W::T;
+  constexpr int R1 = W::R1, R2 = W::R2, P = W::P, NZ = W::NZ, CPW = W::CPW, T = W::T, NW = W::NW;
   static_assert(W::ok, "k_zw needs T | 32");
   extern __shared__ __align__(16) unsigned char zw_raw[];
   const unsigned raw = smem_addr(zw_raw);
@@ -589,25 +606,31 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   float2* xs = reinterpret_cast<float2*>(base + W::off_x);
   float2* twa = reinterpret_cast<float2*>(base + W::off_twa);
   float2* twb = reinterpret_cast<float2*>(base + W::off_twb);
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);   // [2]: a view's tile has landed
+  uint64_t* done = full + 2;                                          // [2]: the compute warps are done with it
   __shared__ int s_list[kMaxLaunchSlots];
   __shared__ int s_ws[32];
+  __shared__ int s_abort;
   const int nact = build_active(a.sel, s_list, s_ws);
   if (nact == 0) return;
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   const int ncont = 2 * a.nx;
   const int tiles_c = ncont / P;
   const int ky = blockIdx.x / tiles_c;
   const int kx0 = (blockIdx.x % tiles_c) * P;
-  const int lane = tid & 31;
-  const int t = lane / CPW;
-  const int c = (tid >> 5) * CPW + lane % CPW;
-  if (tid == 0) {
+  const bool producer = warp == NW;
+  if (producer && lane == 0) {
+    s_abort = 0;
     mbar_init(&full[0], 1);
     mbar_init(&full[1], 1);
+    mbar_init(&done[0], NW);
+    mbar_init(&done[1], NW);
     mbar_init_fence();
-    mbar_expect_tx(&full[0], (unsigned)W::stage_bytes);
-    tma_load_4d(stage, &a.tmap, &full[0], 2 * kx0, ky, 0, a.slot0 + s_list[0]);
+    for (int k = 0; k < 2 && k < nact; ++k) {
+      mbar_expect_tx(&full[k], (unsigned)W::stage_bytes);
+      tma_load_4d(stage + (size_t)k * NZ * P, &a.tmap, &full[k], 2 * kx0, ky, 0, a.slot0 + s_list[k]);
+    }
   }
   // Ghat tile with kz folded into [0, NZ] (Ghat is even in every axis), and the stage twiddles
   const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
@@ -621,23 +644,46 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
     twb[(i / R2) * W::TWB + i % R2] = __ldg(a.zwb + i);
   }
   __syncthreads();
+  if (producer) {
+    // producer: after the compute warps release a view's buffer, store it and refill it with the
+    // view two ahead
+    if (lane != 0) return;
+    int iv = 0;
+    for (; iv < nact; ++iv) {
+      const int buf = iv & 1;
+      if (!mbar_wait_abort(&done[buf], (unsigned)(iv >> 1) & 1u, &s_abort)) break;
+      float2* sb = stage + (size_t)buf * NZ * P;
+      tma_store_4d(&a.tmap, sb, 2 * kx0, ky, 0, a.slot0 + s_list[iv]);
+      bulk_commit();
+      if (iv + 2 < nact) {
+        bulk_wait_read_all();   // the store has read the buffer
+        mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
+        tma_load_4d(sb, &a.tmap, &full[buf], 2 * kx0, ky, 0, a.slot0 + s_list[iv + 2]);
+      }
+    }
+    bulk_wait_read_all();
+    if (iv < nact) {
+      // gave up at view iv: flag it, and give the loads still in flight into this CTA's buffers
+      // (views iv and iv + 1) a bounded time to land
+      atomicExch(a.err, 1);
+      mbar_wait(&full[iv & 1], (unsigned)(iv >> 1) & 1u);
+      if (iv + 1 < nact) mbar_wait(&full[(iv + 1) & 1], (unsigned)((iv + 1) >> 1) & 1u);
+    }
+    return;
+  }
+  // compute warps: each owns CPW whole columns (lane = t * CPW + column)
+  const int t = lane / CPW;
+  const int c = warp * CPW + lane % CPW;
   float2* xc = xs + c * W::XP;
   const float2* gc = gs + c;
   // byte offset of (z = t + R2 j, c) in a tile: row base for j = 0, plus j R2 rows
   const unsigned rb = swz128(t, c);
-  int timed_out = 0;
-  int iv = 0;
 #pragma unroll 1
-  for (; iv < nact; ++iv) {
+  for (int iv = 0; iv < nact; ++iv) {
     const int buf = iv & 1;
     const int slot = s_list[iv];
-    if (tid == 0 && iv + 1 < nact) {
-      bulk_wait_read_all();   // the store of view iv-1 has read the buffer that is about to be refilled
-      mbar_expect_tx(&full[buf ^ 1], (unsigned)W::stage_bytes);
-      tma_load_4d(stage + (size_t)(buf ^ 1) * NZ * P, &a.tmap, &full[buf ^ 1], 2 * kx0, ky, 0,
-                  a.slot0 + s_list[iv + 1]);
-    }
-    if (!mbar_wait(&full[buf], (unsigned)(iv >> 1) & 1u)) timed_out = 1;
+    const bool ok = mbar_wait_abort(&full[buf], (unsigned)(iv >> 1) & 1u, &s_abort);
+    if (!__all_sync(0xffffffffu, ok)) break;
     count_run(a.sel);
     unsigned char* sb = reinterpret_cast<unsigned char*>(stage + (size_t)buf * NZ * P);
     float2 u[R2];
@@ -694,21 +740,8 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
         *reinterpret_cast<float2*>(sb + (R2 % 8 == 0 ? rb + R2 * j2 * 128 : swz128(t + R2 * j2, c))) = w[j2];
     }
     fence_async_smem();
-    if (__syncthreads_or(timed_out)) break;
-    if (tid == 0) {
-      tma_store_4d(&a.tmap, sb, 2 * kx0, ky, 0, a.slot0 + slot);
-      bulk_commit();
-    }
-  }
-  if (tid == 0) {
-    bulk_wait_read_all();
-    if (iv < nact) {
-      // gave up in view iv: flag it, and give the copies still in flight into this CTA's buffers
-      // (this view's tile and the prefetch of the next one) a bounded time to land
-      atomicExch(a.err, 1);
-      mbar_wait(&full[iv & 1], (unsigned)(iv >> 1) & 1u);
-      if (iv + 1 < nact) mbar_wait(&full[(iv + 1) & 1], (unsigned)((iv + 1) >> 1) & 1u);
-    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&done[buf]);
   }
 }
 
