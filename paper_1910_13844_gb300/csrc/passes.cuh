@@ -31,12 +31,12 @@ enum FxMode : int { FX_F_TIMES = 0, FX_COPY = 1, FX_BICG_P = 2, FX_BICG_S = 3 };
 enum IxMode : int { IX_STORE = 0, IX_MATVEC = 1, IX_BICG_V = 2, IX_BICG_T = 3, IX_RESID = 4 };
 
 struct SlotSel {
-  const SlotDev* slots;   // null: every slot runs with the defaults below
-  unsigned mask;          // run slot s iff (slots[s].flags & mask) != 0 (mask 0: all)
-  const float* f_default; // potential when slots == null
-  int adj_default;        // adjoint flag when slots == null
-  unsigned long long* runs;  // if set: +1 per slot that ran (counted by its first CTA)
-  int nslots;                // slots covered by this launch
+  const SlotDev* slots = nullptr;      // null: every slot runs with the defaults below
+  unsigned mask = 0;                   // run slot s iff (slots[s].flags & mask) != 0 (mask 0: all)
+  const float* f_default = nullptr;    // potential when slots == null
+  int adj_default = 0;                 // adjoint flag when slots == null
+  unsigned long long* runs = nullptr;  // if set: +1 per slot that ran (counted by its first CTA)
+  int nslots = 0;                      // slots covered by this launch
 };
 
 // Upper bound on the views of one call (slot tables are sized by it).
