@@ -124,8 +124,9 @@ Z_SOURCES = ["paper_1910_13844_gb300/csrc/passes.cuh", "paper_1910_13844_gb300/c
              "paper_1910_13844_gb300/csrc/common.cuh"]
 
 
-def traffic_per_slot(kernel: str):
-    """ncu DRAM bytes per slot for `kernel`, if recorded for the current source (else None)."""
+def traffic_per_slot(kernel: str, field: str = "dram_bytes_per_slot"):
+    """An ncu figure per slot for `kernel` (DRAM bytes, or FP32 pipe lane operations), if recorded for
+    the current source (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as fh:
@@ -133,9 +134,22 @@ def traffic_per_slot(kernel: str):
     except Exception:
         return None
     rec = d.get(kernel)
-    if not rec or rec.get("source_hash") != source_hash(Z_SOURCES):
+    if not rec or rec.get("source_hash") != source_hash(Z_SOURCES) or field not in rec:
         return None
-    return float(rec["dram_bytes_per_slot"])
+    return float(rec[field])
+
+
+def alu_roofline(ops_per_view, launch_ms, views_per_launch, sm_mhz):
+    """The z pass against GB300's FP32 pipe (it performs ~8 flop per byte and is bound by FP32 issue,
+    not HBM): FP32 lane operations per view from ncu's opcode counts (FADD2 counted twice, FFMA and
+    FMUL once) over the live launch time; peak = 152 SMs x 128 FP32 lanes x the SM clock under load."""
+    if not ops_per_view or not launch_ms or not sm_mhz:
+        return None
+    achieved = ops_per_view * views_per_launch / (launch_ms / 1e3) / 1e12
+    peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+    return {"kernel": "k_zw", "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2),
+            "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4),
+            "ops_per_view": int(ops_per_view), "peak_source": "152 SMs x 128 FP32 lanes x median SM clock"}
 
 
 def dist_env():
@@ -375,6 +389,8 @@ def run_gpu(args):
             "algorithmic_bytes_per_launch": int(bytes_per_launch),
             "launch_ms": round(z_ms_launch, 4), "active_views_per_launch": round(active_per_launch, 2),
         },
+        "roofline_alu": alu_roofline(traffic_per_slot("z_pass", "fp32_lane_ops_per_slot"), z_ms_launch,
+                                     active_per_launch, clocks.summary().get("sm_mhz")),
         "matvec": {
             "gbs": round(mv_bytes / (mv_ms / 1e3) / 1e9, 1) if mv_ms else None,
             "frac_hbm": round(mv_bytes / (mv_ms / 1e3) / 1e9 / peak, 4) if mv_ms else None,
