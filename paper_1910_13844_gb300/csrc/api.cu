@@ -74,8 +74,10 @@ static int make_twiddles(int L, int R1, int R2, float2** tw, float2** tw2) {
       const int j = (k1 * n2) % L;
       b[k1 * R2 + n2] = a[j];
     }
-  LS_CUDA_TRY(cudaMalloc(tw, L * sizeof(float2)));
-  LS_CUDA_TRY(cudaMemcpy(*tw, a.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
+  if (tw) {
+    LS_CUDA_TRY(cudaMalloc(tw, L * sizeof(float2)));
+    LS_CUDA_TRY(cudaMemcpy(*tw, a.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   if (tw2) {
     LS_CUDA_TRY(cudaMalloc(tw2, L * sizeof(float2)));
     LS_CUDA_TRY(cudaMemcpy(*tw2, b.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
@@ -258,7 +260,6 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   z.nx = P->nx; z.ny = P->ny; z.nz = P->nz;
   z.a2 = e.a2; z.a2_stride = e.a2_stride;
   z.gocta = P->gocta;
-  z.tw = P->tw_z;
   z.twa = P->twa_z;
   z.twb = P->twb_z;
   z.zwa = P->zwa_z;
@@ -470,7 +471,7 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   v.nx = P->nx; v.ny = P->ny; v.nz = P->nz; v.N = P->N; v.kb = P->kb; v.h = P->h; v.opt = P->opt;
   v.mx = P->mx; v.my = P->my; v.ox = P->ox; v.oy = P->oy; v.x_gamma = P->x_gamma;
   v.px = P->px; v.py = P->py; v.pz = P->pz;
-  v.tw_x = P->tw_x; v.tw2_x = P->tw2_x; v.tw_y = P->tw_y; v.tw_z = P->tw_z;
+  v.tw2_x = P->tw2_x; v.tw_y = P->tw_y;
   v.twa_z = P->twa_z; v.twb_z = P->twb_z; v.zwa_z = P->zwa_z; v.zwb_z = P->zwb_z;
   v.gocta = P->gocta; v.k2hat = P->k2hat; v.p_built = P->p_built;
   const Engine& e = P->eng;
@@ -498,7 +499,7 @@ ls_plan* plan_clone_shared(const ls_plan* P) {
   c->nx = P->nx; c->ny = P->ny; c->nz = P->nz; c->N = P->N; c->kb = P->kb; c->h = P->h; c->opt = P->opt;
   c->mx = P->mx; c->my = P->my; c->ox = P->ox; c->oy = P->oy; c->x_gamma = P->x_gamma;
   c->px = P->px; c->py = P->py; c->pz = P->pz;
-  c->tw_x = P->tw_x; c->tw2_x = P->tw2_x; c->tw_y = P->tw_y; c->tw_z = P->tw_z;
+  c->tw2_x = P->tw2_x; c->tw_y = P->tw_y;
   c->twa_z = P->twa_z; c->twb_z = P->twb_z; c->zwa_z = P->zwa_z; c->zwb_z = P->zwb_z;
   c->gocta = P->gocta; c->k2hat = P->k2hat; c->p_built = P->p_built;
   c->owns_shared = false;
@@ -745,9 +746,8 @@ int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel, c
     delete P;
     return LS_ECUDA;
   }
-  rc = make_twiddles(L[0], P->px.r1, P->px.r2, &P->tw_x, &P->tw2_x);
+  rc = make_twiddles(L[0], P->px.r1, P->px.r2, nullptr, &P->tw2_x);
   if (rc == LS_OK) rc = make_twiddles(L[1], P->py.r1, P->py.r2, &P->tw_y, nullptr);
-  if (rc == LS_OK) rc = make_twiddles(L[2], P->pz.r1, P->pz.r2, &P->tw_z, nullptr);
   if (rc == LS_OK) rc = make_z_twiddles(L[2], P->pz.r1, P->pz.r2, &P->twa_z, &P->twb_z);
   if (rc == LS_OK) {
     if (P->pz.zr1 == P->pz.r1) {
@@ -794,7 +794,7 @@ void ls_plan_destroy(ls_plan* P) {
   engine_release(P->eng);
   cudaFree(P->pupil_h);
   if (P->owns_shared) {
-    cudaFree(P->tw_x); cudaFree(P->tw2_x); cudaFree(P->tw_y); cudaFree(P->tw_z);
+    cudaFree(P->tw2_x); cudaFree(P->tw_y);
     if (P->zwa_z != P->twa_z) { cudaFree(P->zwa_z); cudaFree(P->zwb_z); }
     cudaFree(P->twa_z); cudaFree(P->twb_z);
     cudaFree(P->gocta); cudaFree(P->k2hat);

@@ -63,7 +63,7 @@ struct ls_plan {
   int mx = 0, my = 0, ox = 0, oy = 0;
   double x_gamma = 0;
   lsgpu::PassLaunch px{}, py{}, pz{};
-  float2 *tw_x = nullptr, *tw2_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
+  float2 *tw2_x = nullptr, *tw_y = nullptr;   // x-pass stage twiddles [k1*R2 + n2]; y-pass exp(-2 pi i j / L)
   float2 *twa_z = nullptr, *twb_z = nullptr;
   float2 *zwa_z = nullptr, *zwb_z = nullptr;   // z tables for the TMA-staged split (alias twa_z/twb_z if equal)
   float2* gocta = nullptr;

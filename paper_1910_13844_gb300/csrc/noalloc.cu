@@ -109,7 +109,6 @@ extern "C" int ls_matvec_noalloc(const ls_plan* P, const float* f, const ls_c64*
   z.nx = P->nx; z.ny = P->ny; z.nz = P->nz;
   z.a2 = a2; z.a2_stride = a2n;
   z.gocta = P->gocta;
-  z.tw = P->tw_z;
   z.twa = P->twa_z;
   z.twb = P->twb_z;
   z.zwa = P->zwa_z;

@@ -73,7 +73,6 @@ struct ZParams {
   int nx, ny, nz;              // A2 is [nz][2ny][2nx]
   float2* a2; size_t a2_stride;
   const float2* gocta;         // [(nz+1)][(ny+1)][(nx+1)], scaled by 1/(8 nx ny nz)
-  const float2* tw;
   const float2* twa;           // twa[t*R1 + k1] = exp(-2 pi i t k1 / L), t < R2 (forward split)
   const float2* twb;           // twb[t*R2 + j1] = exp(-2 pi i t j1 / L), t < R1 (transposed split)
   const float2* zwa;           // the same two tables for the split of the TMA-staged pass (ZRadix)
