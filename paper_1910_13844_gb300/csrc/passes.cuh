@@ -213,7 +213,7 @@ __device__ __forceinline__ void block_sum_store(float (&acc)[NV], double* out) {
 
 // ------------------------------------------------------------------------- FX
 template <int L>
-__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_fx(FxParams a) {
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 6) k_fx(FxParams a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
