@@ -88,6 +88,18 @@ typedef struct {
 
 typedef struct ls_plan ls_plan;
 
+/* Launch variants chosen by ls_autotune (no counterpart in the paper). */
+typedef struct {
+  int z_tma;              /* 1: TMA-staged z pass with warp-local exchanges; 0: cp.async-staged            */
+  int ix_prefetch;        /* 1: the last pass asks L2 for its epilogue operands at kernel start            */
+  int fx_views_fastest;   /* 1: first-pass grid with the views fastest (shared potential rows from L2)      */
+  int check_every;        /* BiCGStab iterations between host reads of the convergence mask                */
+  int use_graphs;         /* 1: iterations replayed from a captured CUDA graph                              */
+  double matvec_us_per_view;  /* batched operator application with the chosen variants, per view (µs)      */
+  double solve_ms;            /* forward solve of the tuning batch with the chosen variants (ms)            */
+  int from_cache;             /* 1: read from the LS_AUTOTUNE_CACHE file, nothing was timed                  */
+} ls_tune;
+
 /* Fill *opt with the defaults listed above. */
 void ls_default_options(ls_options* opt);
 
@@ -208,6 +220,14 @@ int ls_prox_tv(const ls_grid* grid, const float* z, float* x, double lam, int it
  * stream.  lam <= 0 gives max(z, 0).  Asynchronous on cuda_stream. */
 int ls_prox_hs(const ls_grid* grid, const float* z, float* x, double lam, int iters, float* work,
                void* cuda_stream);
+
+/* Times the launch variants of ls_tune on this plan's grid with n_views plane-wave views of the
+ * potential f (device, N floats), one knob after the other, and keeps the fastest in the plan (the
+ * plan's check_every / use_graphs options are overwritten).  If the environment variable
+ * LS_AUTOTUNE_CACHE names a file, a result for the same device, grid and view count is read from it
+ * instead of timing, and new results are appended to it.  Synchronous; uses the plan's workspace
+ * (its contents are overwritten).  out may be NULL.  No counterpart in the paper. */
+int ls_autotune(ls_plan* plan, int n_views, const float* f, ls_tune* out, void* cuda_stream);
 
 /* Incident fields from their measurement on the detector plane (Sec. 3.4): for every plane z of
  * the volume, u_in(., z) = p_z * y_in with p_hat_z(w) = exp(-i (x_gamma - z) sqrt(k_b^2 - |w|^2))

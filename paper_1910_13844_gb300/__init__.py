@@ -28,7 +28,7 @@ __all__ = [
     "ls_farfield_adjoint", "ls_residual", "ls_gradient", "ls_server_create", "ls_submit", "ls_poll",
     "ls_server_destroy", "ls_status_string", "ls_last_error", "ls_workspace_bytes", "ls_profile", "library_path",
     "ls_matvec_noalloc", "ls_matvec_batch", "Server", "ls_set_pupil", "ls_apply_pupil", "ls_incident_field",
-    "ls_forward_warm", "ls_prox_tv", "ls_prox_hs",
+    "ls_forward_warm", "ls_prox_tv", "ls_prox_hs", "ls_autotune",
 ]
 
 _SOFT = (LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN, LS_TIMEOUT, LS_PENDING)
@@ -230,6 +230,16 @@ def ls_prox_hs(z, x, lam: float, iters: int = 20, work=None, stream=None) -> int
                                   _ptr(work) if work is not None else None, _stream(stream)), "ls_prox_hs")
 
 
+def ls_autotune(plan: int, n_views: int, f, stream=None) -> dict:
+    """Time the plan's launch variants for batches of n_views views of f and keep the fastest.
+
+    Returns the chosen variants and timings (ls_tune as a dict).  With LS_AUTOTUNE_CACHE set to a
+    file name, results are read from / appended to that file."""
+    t = _abi.ls_tune()
+    _check(_lib.ls_autotune(plan, int(n_views), _ptr(f), C.byref(t), _stream(stream)), "ls_autotune")
+    return t.as_dict()
+
+
 def ls_farfield(plan: int, f, u, far, stream=None) -> int:
     a_u, n = _views(u)
     a_far, _ = _views(far)
@@ -347,6 +357,9 @@ class Plan:
         far = self.detector(q) if want_far else None
         code, stats = ls_forward(self.handle, f, u_in, u, far, stream)
         return u, far, code, stats
+
+    def autotune(self, n_views: int, f, stream=None) -> dict:
+        return ls_autotune(self.handle, n_views, f, stream)
 
     def gradient(self, f, residuals, u_fwd=None, u_in=None, weights=None, stream=None):
         g = torch.empty(self.shape, dtype=torch.float32, device=f.device)

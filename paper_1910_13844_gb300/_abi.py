@@ -64,6 +64,15 @@ class ls_result(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations_max", C.c_int), ("submit_to_done_ms", C.c_double)]
 
 
+class ls_tune(C.Structure):
+    _fields_ = [("z_tma", C.c_int), ("ix_prefetch", C.c_int), ("fx_views_fastest", C.c_int),
+                ("check_every", C.c_int), ("use_graphs", C.c_int), ("matvec_us_per_view", C.c_double),
+                ("solve_ms", C.c_double), ("from_cache", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _P = C.c_void_p
 _PP = C.POINTER(C.c_void_p)
 
@@ -99,6 +108,7 @@ SIGNATURES = {
     "ls_set_pupil": (C.c_int, [_P, C.c_double, C.c_double]),
     "ls_apply_pupil": (C.c_int, [_P, C.c_int, _PP, _PP, C.c_int, _P]),
     "ls_incident_field": (C.c_int, [_P, C.c_int, _PP, C.POINTER(C.c_double), _PP, _P]),
+    "ls_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(ls_tune), _P]),
 }
 
 _lib = None

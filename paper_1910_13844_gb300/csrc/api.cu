@@ -219,6 +219,7 @@ static FxParams fx_base(ls_plan* P, SlotSel sel, int rows) {
   a.dst = P->eng.a1;
   a.dst_stride = P->eng.a1_stride;
   a.tw2 = P->tw2_x;
+  a.views_fastest = P->tune_fx_views_fastest;
   return a;
 }
 
@@ -253,7 +254,7 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   timed(P, LS_K_FY, nslots, st, [&] { P->py.fy(fy, nslots, st); });
   ZParams z = {};
   z.tmap = e.a2_map;
-  z.use_tma = e.a2_map_ok;
+  z.use_tma = e.a2_map_ok && P->tune_z_tma;
   z.slot0 = e.slot0;
   z.err = e.counts_d + 4;
   z.sel = counted(P, sel, LS_K_Z);
@@ -274,6 +275,7 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   ix.rows = P->ny * P->nz;
   ix.src = e.a1; ix.src_stride = e.a1_stride;
   ix.tw2 = P->tw2_x;
+  ix.prefetch = P->tune_ix_prefetch;
   timed(P, LS_K_IX, nslots, st, [&] { P->px.ix(ix, nslots, st); });
 }
 
@@ -445,12 +447,15 @@ void seq_far_adjoint(ls_plan* P, int nslots, const float2* const* r_dev_table, u
   ix.vstride = e.N;
   ix.out_o = 0; ix.out_m = P->nx;
   ix.tw2 = P->tw2_x;
+  ix.prefetch = P->tune_ix_prefetch;
   timed(P, LS_K_IX, nslots, st, [&] { P->px.ix(ix, nslots, st); });
 }
 
 int ensure_iter_graph(ls_plan* P, int nslots) {
   Engine& e = P->eng;
-  if (e.iter_graph && e.iter_graph_slots == nslots) return LS_OK;
+  // the captured launches carry the plan's launch variants: recapture when ls_autotune changed them
+  const int variant = P->tune_z_tma | P->tune_ix_prefetch << 1 | P->tune_fx_views_fastest << 2;
+  if (e.iter_graph && e.iter_graph_slots == nslots && e.iter_graph_variant == variant) return LS_OK;
   if (e.iter_graph) {
     cudaGraphExecDestroy(e.iter_graph);
     e.iter_graph = nullptr;
@@ -463,6 +468,7 @@ int ensure_iter_graph(ls_plan* P, int nslots) {
   cudaGraphDestroy(g);
   LS_CUDA_TRY(err);
   e.iter_graph_slots = nslots;
+  e.iter_graph_variant = variant;
   return LS_OK;
 }
 
@@ -474,6 +480,8 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   v.tw2_x = P->tw2_x; v.tw_y = P->tw_y;
   v.twa_z = P->twa_z; v.twb_z = P->twb_z; v.zwa_z = P->zwa_z; v.zwb_z = P->zwb_z;
   v.gocta = P->gocta; v.k2hat = P->k2hat; v.p_built = P->p_built;
+  v.tune_z_tma = P->tune_z_tma; v.tune_ix_prefetch = P->tune_ix_prefetch;
+  v.tune_fx_views_fastest = P->tune_fx_views_fastest;
   const Engine& e = P->eng;
   Engine& w = v.eng;
   w = e;
@@ -502,8 +510,40 @@ ls_plan* plan_clone_shared(const ls_plan* P) {
   c->tw2_x = P->tw2_x; c->tw_y = P->tw_y;
   c->twa_z = P->twa_z; c->twb_z = P->twb_z; c->zwa_z = P->zwa_z; c->zwb_z = P->zwb_z;
   c->gocta = P->gocta; c->k2hat = P->k2hat; c->p_built = P->p_built;
+  c->tune_z_tma = P->tune_z_tma; c->tune_ix_prefetch = P->tune_ix_prefetch;
+  c->tune_fx_views_fastest = P->tune_fx_views_fastest;
   c->owns_shared = false;
   return c;
+}
+
+int tune_matvec(ls_plan* P, const float* f, int n, cudaStream_t st) {
+  Engine& e = P->eng;
+  for (int q = 0; q < n; ++q) {
+    slot_defaults(P, e.slots_h[q], f, 0);
+    e.slots_h[q].flags = SLOT_AUX;
+  }
+  LS_CUDA_TRY(cudaMemcpyAsync(e.slots_d, e.slots_h, (size_t)n * sizeof(SlotDev), cudaMemcpyHostToDevice, st));
+  SlotSel sel = sel_slots(P, SLOT_AUX);
+  FxParams fx = fx_base(P, sel, P->ny * P->nz);
+  fx.mode = FX_F_TIMES;
+  fx.src = e.vptr(V_X);
+  IxParams ix;
+  memset(&ix, 0, sizeof(ix));
+  ix.mode = IX_MATVEC;
+  ix.in0 = e.vptr(V_X);
+  ix.out0 = e.vptr(V_R);
+  ix.vstride = e.N;
+  matvec_core(P, sel, n, fx, ix, st);
+  LS_CUDA_TRY(cudaGetLastError());
+  return LS_OK;
+}
+
+int tune_forward(ls_plan* P, const float* f, int n, cudaStream_t st) {
+  Engine& e = P->eng;
+  LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_X), e.vptr(V_B), (size_t)n * e.N * sizeof(float2), cudaMemcpyDeviceToDevice,
+                              st));
+  for (int q = 0; q < n; ++q) slot_defaults(P, e.slots_h[q], f, 0);
+  return engine_solve(P, n, st);
 }
 
 int engine_solve(ls_plan* P, int nslots, cudaStream_t st) {

@@ -1,0 +1,192 @@
+// Launch-variant autotuner.  For one plan and batch size it times the variants that the passes and
+// the solve loop can switch between at run time, on the plan's own grid and views:
+//   * the z pass: TMA-staged with warp-local exchanges, or cp.async-staged with CTA-wide exchanges;
+//   * IX: L2 prefetch of its epilogue operands at kernel start, or not;
+//   * FX: launch grid with the views fastest (shared potential rows from L2), or the rows fastest;
+//   * the solve loop: iterations between host reads of the convergence mask (2, 4, 8), and replay
+//     of the iteration from a captured CUDA graph or direct launches.
+// Operator variants are timed on batched operator applications, the loop variants on forward solves
+// of plane-wave illuminations.  One knob is tuned at a time, in the order above, keeping the best
+// value of the earlier ones.  Results can be cached in a text file (LS_AUTOTUNE_CACHE) keyed by the
+// device name, the grid and the number of views.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "engine.h"
+
+namespace lsgpu {
+
+static std::mutex g_cache_mu;
+
+static std::string tune_key(const ls_plan* P, int n_views) {
+  cudaDeviceProp prop;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "unknown";
+  for (char& ch : name)
+    if (ch == ' ') ch = '_';
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s:%dx%dx%d:%d", name.c_str(), P->nx, P->ny, P->nz, n_views);
+  return buf;
+}
+
+static bool cache_lookup(const std::string& key, ls_tune* t) {
+  const char* path = getenv("LS_AUTOTUNE_CACHE");
+  if (!path || !*path) return false;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  FILE* fp = fopen(path, "r");
+  if (!fp) return false;
+  char k[256];
+  ls_tune v;
+  bool found = false;
+  while (fscanf(fp, "%255s %d %d %d %d %d %lf %lf", k, &v.z_tma, &v.ix_prefetch, &v.fx_views_fastest,
+                &v.check_every, &v.use_graphs, &v.matvec_us_per_view, &v.solve_ms) == 8)
+    if (key == k) { *t = v; found = true; }   // the last entry for a key wins
+  fclose(fp);
+  return found;
+}
+
+static void cache_store(const std::string& key, const ls_tune& t) {
+  const char* path = getenv("LS_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  FILE* fp = fopen(path, "a");
+  if (!fp) return;
+  fprintf(fp, "%s %d %d %d %d %d %.9g %.9g\n", key.c_str(), t.z_tma, t.ix_prefetch, t.fx_views_fastest,
+          t.check_every, t.use_graphs, t.matvec_us_per_view, t.solve_ms);
+  fclose(fp);
+}
+
+static void apply(ls_plan* P, const ls_tune& t) {
+  P->tune_z_tma = t.z_tma;
+  P->tune_ix_prefetch = t.ix_prefetch;
+  P->tune_fx_views_fastest = t.fx_views_fastest;
+  P->opt.check_every = t.check_every;
+  P->opt.use_graphs = t.use_graphs;
+}
+
+// mean milliseconds of `reps` calls of fn after one untimed call; negative on error
+template <typename F>
+static double time_ms(cudaStream_t st, int reps, F fn) {
+  if (fn() != LS_OK) return -1.0;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return -1.0;
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1.0; }
+  cudaEventRecord(a, st);
+  int rc = LS_OK;
+  for (int r = 0; r < reps && rc == LS_OK; ++r) rc = fn();
+  cudaEventRecord(b, st);
+  float ms = -1.f;
+  if (rc == LS_OK && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc == LS_OK && ms >= 0.f ? ms / reps : -1.0;
+}
+
+}  // namespace lsgpu
+
+using namespace lsgpu;
+
+extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out, void* stream) {
+  if (!P || !f || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const std::string key = tune_key(P, n_views);
+  // the workspace (and with it the z pass's TMA map) must exist before a variant is chosen
+  int rc = engine_reserve(P, n_views);
+  if (rc) return rc;
+  ls_tune best;
+  if (cache_lookup(key, &best)) {
+    if (!P->eng.a2_map_ok) best.z_tma = 0;
+    apply(P, best);
+    best.from_cache = 1;
+    if (out) *out = best;
+    return LS_OK;
+  }
+  Engine& e = P->eng;
+  // plane-wave right-hand sides on a cone of half-angle asin(0.6) around z (numerical aperture 0.8 in
+  // water), one direction per view
+  std::vector<double> k(3 * (size_t)n_views);
+  for (int q = 0; q < n_views; ++q) {
+    const double phi = 2.0 * 3.14159265358979323846 * q / n_views, s = 0.6;
+    k[3 * q] = P->kb * s * cos(phi);
+    k[3 * q + 1] = P->kb * s * sin(phi);
+    k[3 * q + 2] = P->kb * sqrt(1.0 - s * s);
+  }
+  std::vector<void*> ptrs(n_views);
+  for (int q = 0; q < n_views; ++q) ptrs[q] = e.vptr(V_B, q);
+  LS_CUDA_TRY(cudaMemcpyAsync(e.kvec_d, k.data(), k.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  rc = engine_upload_ptrs(P, 0, (const void* const*)ptrs.data(), n_views, st);
+  if (rc) return rc;
+  PlaneWaveParams pw{P->nx, P->ny, P->nz, P->h, e.kvec_d, (float2* const*)engine_ptr_table(P, 0)};
+  LS_CUDA_TRY(launch_plane_waves(pw, n_views, st));
+  LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_X), e.vptr(V_B), (size_t)n_views * e.N * sizeof(float2),
+                              cudaMemcpyDeviceToDevice, st));
+  // the per-launch profiler stays off while timing (it would also disable graph replay)
+  const bool prof = P->prof.on;
+  P->prof.on = false;
+  ls_tune cur;
+  cur.z_tma = e.a2_map_ok ? 1 : 0;
+  cur.ix_prefetch = 1;
+  cur.fx_views_fastest = 1;
+  cur.check_every = P->opt.check_every > 0 ? P->opt.check_every : 4;
+  cur.use_graphs = 1;
+  cur.from_cache = 0;
+  auto matvec = [&] { return tune_matvec(P, f, n_views, st); };
+  auto tune_op = [&](int* knob, int n_values, const int* values) -> double {
+    double best_ms = -1.0;
+    int best_v = *knob;
+    for (int i = 0; i < n_values; ++i) {
+      *knob = values[i];
+      apply(P, cur);
+      const double ms = time_ms(st, 3, matvec);
+      if (ms > 0 && (best_ms < 0 || ms < best_ms)) { best_ms = ms; best_v = values[i]; }
+    }
+    *knob = best_v;
+    apply(P, cur);
+    return best_ms;
+  };
+  static const int two[2] = {1, 0};
+  double mv_ms = -1.0;
+  if (e.a2_map_ok) mv_ms = tune_op(&cur.z_tma, 2, two);
+  mv_ms = tune_op(&cur.ix_prefetch, 2, two);
+  mv_ms = tune_op(&cur.fx_views_fastest, 2, two);
+  // solve loop: forward solves of the plane waves
+  auto solve = [&] { return tune_forward(P, f, n_views, st); };
+  double sv_ms = -1.0;
+  {
+    static const int chunks[3] = {4, 2, 8};
+    int best_v = cur.check_every;
+    for (int c : chunks) {
+      cur.check_every = c;
+      apply(P, cur);
+      const double ms = time_ms(st, 1, solve);
+      if (ms > 0 && (sv_ms < 0 || ms < sv_ms)) { sv_ms = ms; best_v = c; }
+    }
+    cur.check_every = best_v;
+    int best_g = 1;
+    double best_g_ms = -1.0;
+    for (int g : two) {
+      cur.use_graphs = g;
+      apply(P, cur);
+      const double ms = time_ms(st, 1, solve);
+      if (ms > 0 && (best_g_ms < 0 || ms < best_g_ms)) { best_g_ms = ms; best_g = g; }
+    }
+    cur.use_graphs = best_g;
+    if (best_g_ms > 0) sv_ms = best_g_ms;
+  }
+  apply(P, cur);
+  P->prof.on = prof;
+  LS_CUDA_TRY(cudaGetLastError());
+  if (mv_ms < 0 || sv_ms < 0) { set_last_error("autotune timing failed"); return LS_ECUDA; }
+  cur.matvec_us_per_view = 1e3 * mv_ms / n_views;
+  cur.solve_ms = sv_ms;
+  cache_store(key, cur);
+  if (out) *out = cur;
+  return LS_OK;
+}

@@ -39,6 +39,7 @@ struct Engine {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t iter_graph = nullptr;
   int iter_graph_slots = 0;
+  int iter_graph_variant = 0;   // launch variants the graph was captured with
   float2* vptr(int v, int slot = 0) const { return vec + ((size_t)v * cap + slot) * N; }
 };
 
@@ -71,6 +72,10 @@ struct ls_plan {
   int p_built = 0;
   bool owns_shared = true;   // false for clones that borrow another plan's spectra and twiddles
   double2* pupil_h = nullptr; // pupil / refocus transfer function on the 2my x 2mx detector grid (ls_set_pupil)
+  // launch variants chosen by ls_autotune (defaults: the best measured at 128^3 x 60 views)
+  int tune_z_tma = 1;           // TMA-staged z pass where available (else the cp.async-staged one)
+  int tune_ix_prefetch = 1;     // IX asks L2 for its epilogue operands at kernel start
+  int tune_fx_views_fastest = 1;  // FX grid with views fastest
   lsgpu::Engine eng;
   lsgpu::Profiler prof;
 };
@@ -98,6 +103,10 @@ ls_plan plan_slot_view(const ls_plan* P, int s0);
 // New plan object with its own (empty) workspace that shares P's Green spectrum, far-field
 // kernels and twiddles; P must outlive it.
 ls_plan* plan_clone_shared(const ls_plan* P);
+// one batched operator application y = x - G(f x) over slots [0, n) (x in V_X, y in V_R), for the autotuner
+int tune_matvec(ls_plan* P, const float* f, int n, cudaStream_t st);
+// a forward solve of slots [0, n) from the right-hand sides already in V_B (x0 = b), for the autotuner
+int tune_forward(ls_plan* P, const float* f, int n, cudaStream_t st);
 // P y (adjoint: P^H y) for one detector field; scratch holds 4 my mx double2
 int apply_pupil_device(ls_plan* P, const float2* in, float2* out, int adjoint, double2* scratch, cudaStream_t st);
 

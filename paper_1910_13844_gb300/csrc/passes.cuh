@@ -54,6 +54,7 @@ struct FxParams {
   float2* dst;                 // [rows][2nx]
   size_t dst_stride;
   const float2* tw2;           // tw2[k1*R2 + n2] = exp(-2 pi i n2 k1 / L)
+  int views_fastest = 0;       // launch grid (slots, row blocks) instead of (row blocks, slots) (autotuned)
 };
 
 struct StridedParams {
@@ -95,6 +96,7 @@ struct IxParams {
   int out_o, out_m;            // STORE: output window [out_o, out_o+out_m) of x; out rows are out_m long
   double* partials;            // [slot][gridDim.x][4]
   const float2* tw2;
+  int prefetch = 0;            // ask L2 for the epilogue operands at kernel start (autotuned)
 };
 
 __device__ __forceinline__ bool slot_runs(const SlotSel& s, int slot) {
@@ -217,14 +219,15 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 6) k_fx(FxParams a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
-  // slots vary fastest in launch order, so the CTAs of all views that share a row block (and the
-  // potential's rows, common to the views of one sample) run together and f is read from L2
-  const int slot = blockIdx.x;
+  // with views_fastest the CTAs of all views that share a row block (and the potential's rows,
+  // common to the views of one sample) run together and f is read from L2
+  const int slot = a.views_fastest ? blockIdx.x : blockIdx.y;
+  const int rb = a.views_fastest ? blockIdx.y : blockIdx.x;
   if (!slot_runs(a.sel, slot)) return;
-  count_run_if(a.sel, blockIdx.y == 0);
+  count_run_if(a.sel, rb == 0);
   const int t = threadIdx.x, p = threadIdx.y;
   const int nx = L / 2;
-  const int row = blockIdx.y * G::PC + p;
+  const int row = rb * G::PC + p;
   const bool valid = row < a.rows;
   const size_t voff = (size_t)slot * a.vstride + (size_t)row * nx;
   const float* f = slot_f(a.sel, slot);
@@ -763,7 +766,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
   const bool valid = row < a.rows;
   // the epilogue's operands are read after both transforms: ask L2 for their lines now (one
   // 128-byte line per thread and vector; a row holds nx/16 lines)
-  if (valid && a.mode != IX_STORE) {
+  if (a.prefetch && valid && a.mode != IX_STORE) {
     constexpr int lines = (L / 2) / 16;
     const size_t voff0 = (size_t)slot * a.vstride + (size_t)row * nx;
     if (t < lines) prefetch_l2(a.in0 + voff0 + 16 * t);
@@ -853,7 +856,8 @@ template <int L>
 struct PassImpl {
   using G = Geo<L>;
   static void fx(const FxParams& a, int nslots, cudaStream_t st) {
-    dim3 blk(G::T, G::PC), grd(nslots, (a.rows + G::PC - 1) / G::PC);
+    const unsigned rbs = (unsigned)((a.rows + G::PC - 1) / G::PC);
+    dim3 blk(G::T, G::PC), grd = a.views_fastest ? dim3(nslots, rbs) : dim3(rbs, nslots);
     k_fx<L><<<grd, blk, G::smem_contig, st>>>(a);
   }
   static void ix(const IxParams& a, int nslots, cudaStream_t st) {

@@ -66,3 +66,5 @@ def test_argument_errors_are_reported_without_touching_a_gpu(lib):
     assert L.ls_plan_create(ctypes.byref(g), 4, 15.7, 0.0665, None, ctypes.byref(out)) == _abi.LS_EINVAL
     assert L.ls_plan_create(ctypes.byref(g), 2, 15.7, 0.25, None, ctypes.byref(out)) == _abi.LS_EINVAL  # k_b h > pi
     assert b"pi" in L.ls_last_error()
+    t = _abi.ls_tune()
+    assert L.ls_autotune(None, 4, None, ctypes.byref(t), None) == _abi.LS_EINVAL
