@@ -239,6 +239,9 @@ def run_gpu(args):
     y = y + 0.01 * (ynorm / np.sqrt(2 * y[0].numel())).reshape(Q, 1, 1) * noise
     weights = (1.0 / (ynorm.double() ** 2)).cpu().numpy()
 
+    # launch variants for this grid and batch, timed once before the warm-up (outside the timed region)
+    tune = None if args.no_autotune else plan.autotune(Q, f0)
+
     u = plan.field(Q)
     far = plan.detector(Q)
     res = plan.detector(Q)
@@ -309,6 +312,7 @@ def run_gpu(args):
         ls.ls_matvec_batch(plan.handle, f0, uin, u)
     torch.cuda.synchronize()
     iso = ls.ls_profile(plan.handle, False)
+    cufft_us, cufft_diff = cufft_matvec_baseline(torch, ls, plan, f0, uin, u) if rank == 0 else (None, None)
 
     solves_per_step = 2 * Q
     ms_step = ms_total / args.steps
@@ -380,6 +384,8 @@ def run_gpu(args):
             "mean_adjoint_iterations": float(np.mean(stats_acc["adj_iters"])),
             "worst_status": int(max(stats_acc["status"])),
             "parallelism": f"replicas{ws}" if ws > 1 else "single",
+            "autotune": ({k: tune[k] for k in ("z_tma", "ix_prefetch", "fx_views_fastest", "check_every",
+                                               "use_graphs", "from_cache")} if tune else "off (defaults)"),
         },
         "roofline": {
             "kernel": "k_z (z-pencil FFT, Green multiply, inverse FFT, crop)",
@@ -405,6 +411,14 @@ def run_gpu(args):
             "us_per_view": round(1e3 * iso_ms / max(iso["z"][3], 1), 2),
             "pass_gbs": iso_gbs,
             "how": f"ls_matvec_batch over all {Q} views, 5 launches per pass, same byte model",
+        },
+        "cufft_matvec": {
+            "us_per_view": round(cufft_us, 2) if cufft_us else None,
+            "ours_us_per_view": round(1e3 * iso_ms / max(iso["z"][3], 1), 2),
+            "speedup": round(cufft_us / (1e3 * iso_ms / max(iso["z"][3], 1)), 3) if cufft_us and iso_ms else None,
+            "max_rel_diff": cufft_diff,
+            "how": "torch.fft (cuFFT) C2C 3-D on the zero-padded f x, full Green spectrum multiply, inverse, "
+                   "crop, subtract; 10 views per batched transform; timed comparison only",
         },
         "update_gbs": update_gbs,
         "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in prof.items()} if total_kernel_ms else {},
@@ -452,6 +466,43 @@ def serve_requests(n, seed=2026):
         out.append({"shape": shape, "views": int(rng.integers(8, 61)), "grad": bool(rng.random() < 0.3),
                     "seed": int(rng.integers(1 << 30))})
     return out
+
+
+def cufft_matvec_baseline(torch, ls, plan, f, x, y_ours, reps=3, chunk=10):
+    """The same operator x - G(f x) through cuFFT (torch.fft, timed comparison only, never on the product
+    path): zero-pad f x to (2nz, 2ny, 2nx), C2C 3-D FFT, multiply by the full Green spectrum, inverse
+    FFT, crop, subtract -- `chunk` views per batched transform.  Returns microseconds per view and the
+    largest relative L2 difference from the library's result y_ours over the views."""
+    nz, ny, nx = plan.shape
+    Q = x.shape[0]
+    ghat = torch.empty((2 * nz, 2 * ny, 2 * nx), dtype=torch.complex64, device=x.device)
+    ls.ls_green_spectrum(plan.handle, plan.options.oversample_p, ghat)
+    pad = torch.zeros((chunk, 2 * nz, 2 * ny, 2 * nx), dtype=torch.complex64, device=x.device)
+    out = torch.empty_like(x)
+
+    def apply():
+        for q0 in range(0, Q, chunk):
+            c = min(chunk, Q - q0)
+            pad[:c, :nz, :ny, :nx] = f * x[q0:q0 + c]
+            spec = torch.fft.fftn(pad[:c], dim=(-3, -2, -1))
+            spec *= ghat
+            v = torch.fft.ifftn(spec, dim=(-3, -2, -1))
+            out[q0:q0 + c] = x[q0:q0 + c] - v[:, :nz, :ny, :nx]
+
+    apply()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        apply()
+    e1.record()
+    torch.cuda.synchronize()
+    us = 1e3 * e0.elapsed_time(e1) / reps / Q
+    d = torch.linalg.vector_norm((out - y_ours).reshape(Q, -1), dim=1) / \
+        torch.linalg.vector_norm(y_ours.reshape(Q, -1), dim=1)
+    del pad, ghat
+    torch.cuda.empty_cache()
+    return us, float(d.max())
 
 
 def run_serving(torch, ls, n_requests, load=0.8, seed=2026, calib=12):
@@ -672,6 +723,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="bench", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
     ap.add_argument("--serve", action="store_true", help="serving benchmark (Poisson request stream) instead")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 1.0])
