@@ -75,7 +75,7 @@ struct ls_plan {
   // launch variants chosen by ls_autotune (defaults: the best measured at 128^3 x 60 views)
   int tune_z_tma = 1;           // TMA-staged z pass where available (else the cp.async-staged one)
   int tune_ix_prefetch = 1;     // IX asks L2 for its epilogue operands at kernel start
-  int tune_fx_views_fastest = 1;  // FX grid with views fastest
+  int tune_fx_views_fastest = 0;  // FX grid with views fastest (else row blocks fastest)
   lsgpu::Engine eng;
   lsgpu::Profiler prof;
 };
