@@ -680,6 +680,15 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   const float2* gc = gs + c;
   // byte offset of (z = t + R2 j, c) in a tile: row base for j = 0, plus j R2 rows
   const unsigned rb = swz128(t, c);
+  // this thread's Green values (kz = t + R1 k2, the same for every view) stay in registers where
+  // they fit (R2 <= 16); longer splits read them from the shared tile for every view
+  constexpr bool GREG = R2 <= 16;
+  float2 g[GREG ? R2 : 1];
+#pragma unroll
+  for (int k2 = 0; k2 < (GREG ? R2 : 1); ++k2)
+    g[k2] = (GREG && (R1 == T || t < R1))
+                ? (k2 < R2 / 2 ? gc[(t + R1 * k2) * W::GR] : gc[(L - R1 * k2 - t) * W::GR])
+                : make_float2(0.f, 0.f);
 #pragma unroll 1
   for (int iv = 0; iv < nact; ++iv) {
     const int buf = iv & 1;
@@ -713,8 +722,19 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) u[n2] = xc[t * (R2 + 1) + n2];
       Dft<R2, -1>::run(u);
-      if (slot_adj(a.sel, slot)) green_mul<true, R1, R2, L, W::GR>(u, gc, t);
-      else green_mul<false, R1, R2, L, W::GR>(u, gc, t);
+      if constexpr (GREG) {
+        if (slot_adj(a.sel, slot)) {
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmulc(u[k2], g[k2]);
+        } else {
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmul(u[k2], g[k2]);
+        }
+      } else if (slot_adj(a.sel, slot)) {
+        green_mul<true, R1, R2, L, W::GR>(u, gc, t);
+      } else {
+        green_mul<false, R1, R2, L, W::GR>(u, gc, t);
+      }
       // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
       Dft<R2, +1>::run(u);
       const float4* tw4 = reinterpret_cast<const float4*>(twb + t * W::TWB);
