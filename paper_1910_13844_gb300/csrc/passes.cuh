@@ -570,13 +570,20 @@ struct ZW {
   static constexpr int GR = P + CPW;                                          // Ghat row [kz][GR], kz folded to [0, NZ]
   static constexpr int XP = pitch(imax(R1 * (R2 + 1), R2 * (R1 + 1)));        // exchange, padded rows
   static constexpr int TWA = R1 + 2, TWB = R2 + 2;                            // twiddle rows (16-byte aligned)
+  static constexpr int NS = 3;                                                // view buffers (TMA pipeline depth)
+  // each thread's Green values stay in registers across the view loop where they fit (R2 <= 16);
+  // the Green tile is then dead once they are loaded, and the exchange area reuses it
+  static constexpr bool GREG = R2 <= 16;
+  static constexpr size_t r16(size_t b) { return (b + 15) / 16 * 16; }       // every region 16-byte aligned
   static constexpr size_t stage_bytes = (size_t)NZ * P * sizeof(float2);
-  static constexpr size_t off_g = 2 * stage_bytes;
-  static constexpr size_t off_x = off_g + (size_t)(NZ + 1) * GR * sizeof(float2);
-  static constexpr size_t off_twa = off_x + (size_t)P * XP * sizeof(float2);
-  static constexpr size_t off_twb = off_twa + (size_t)R2 * TWA * sizeof(float2);
-  static constexpr size_t off_bar = off_twb + (size_t)R1 * TWB * sizeof(float2);
-  static constexpr size_t smem = off_bar + 4 * sizeof(uint64_t) + 1024;      // + room to align the base to 1024
+  static constexpr size_t g_bytes = r16((size_t)(NZ + 1) * GR * sizeof(float2));
+  static constexpr size_t x_bytes = r16((size_t)P * XP * sizeof(float2));
+  static constexpr size_t off_g = NS * stage_bytes;
+  static constexpr size_t off_x = GREG ? off_g : off_g + g_bytes;
+  static constexpr size_t off_twa = off_x + (GREG ? (g_bytes > x_bytes ? g_bytes : x_bytes) : x_bytes);
+  static constexpr size_t off_twb = off_twa + r16((size_t)R2 * TWA * sizeof(float2));
+  static constexpr size_t off_bar = off_twb + r16((size_t)R1 * TWB * sizeof(float2));
+  static constexpr size_t smem = off_bar + 2 * NS * sizeof(uint64_t) + 1024; // + room to align the base to 1024
 };
 
 // Byte offset of element (z, c) of a [NZ][16] complex64 tile written by TMA with the 128-byte swizzle
@@ -608,8 +615,9 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   float2* xs = reinterpret_cast<float2*>(base + W::off_x);
   float2* twa = reinterpret_cast<float2*>(base + W::off_twa);
   float2* twb = reinterpret_cast<float2*>(base + W::off_twb);
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);   // [2]: a view's tile has landed
-  uint64_t* done = full + 2;                                          // [2]: the compute warps are done with it
+  constexpr int NS = W::NS;
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);   // [NS]: a view's tile has landed
+  uint64_t* done = full + NS;                                         // [NS]: the compute warps are done with it
   __shared__ int s_list[kMaxLaunchSlots];
   __shared__ int s_ws[32];
   __shared__ int s_abort;
@@ -624,12 +632,12 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   const bool producer = warp == NW;
   if (producer && lane == 0) {
     s_abort = 0;
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    mbar_init(&done[0], NW);
-    mbar_init(&done[1], NW);
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&done[k], NW);
+    }
     mbar_init_fence();
-    for (int k = 0; k < 2 && k < nact; ++k) {
+    for (int k = 0; k < NS && k < nact; ++k) {
       mbar_expect_tx(&full[k], (unsigned)W::stage_bytes);
       tma_load_4d(stage + (size_t)k * NZ * P, &a.tmap, &full[k], 2 * kx0, ky, 0, a.slot0 + s_list[k]);
     }
@@ -648,28 +656,27 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   __syncthreads();
   if (producer) {
     // producer: after the compute warps release a view's buffer, store it and refill it with the
-    // view two ahead
+    // view NS ahead
     if (lane != 0) return;
     int iv = 0;
     for (; iv < nact; ++iv) {
-      const int buf = iv & 1;
-      if (!mbar_wait_abort(&done[buf], (unsigned)(iv >> 1) & 1u, &s_abort)) break;
+      const int buf = iv % NS;
+      if (!mbar_wait_abort(&done[buf], (unsigned)(iv / NS) & 1u, &s_abort)) break;
       float2* sb = stage + (size_t)buf * NZ * P;
       tma_store_4d(&a.tmap, sb, 2 * kx0, ky, 0, a.slot0 + s_list[iv]);
       bulk_commit();
-      if (iv + 2 < nact) {
+      if (iv + NS < nact) {
         bulk_wait_read_all();   // the store has read the buffer
         mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
-        tma_load_4d(sb, &a.tmap, &full[buf], 2 * kx0, ky, 0, a.slot0 + s_list[iv + 2]);
+        tma_load_4d(sb, &a.tmap, &full[buf], 2 * kx0, ky, 0, a.slot0 + s_list[iv + NS]);
       }
     }
     bulk_wait_read_all();
     if (iv < nact) {
       // gave up at view iv: flag it, and give the loads still in flight into this CTA's buffers
-      // (views iv and iv + 1) a bounded time to land
+      // (views iv .. iv + NS - 1, all issued) a bounded time to land
       atomicExch(a.err, 1);
-      mbar_wait(&full[iv & 1], (unsigned)(iv >> 1) & 1u);
-      if (iv + 1 < nact) mbar_wait(&full[(iv + 1) & 1], (unsigned)((iv + 1) >> 1) & 1u);
+      for (int j = iv; j < iv + NS && j < nact; ++j) mbar_wait(&full[j % NS], (unsigned)(j / NS) & 1u);
     }
     return;
   }
@@ -682,18 +689,20 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   const unsigned rb = swz128(t, c);
   // this thread's Green values (kz = t + R1 k2, the same for every view) stay in registers where
   // they fit (R2 <= 16); longer splits read them from the shared tile for every view
-  constexpr bool GREG = R2 <= 16;
+  constexpr bool GREG = W::GREG;
   float2 g[GREG ? R2 : 1];
 #pragma unroll
   for (int k2 = 0; k2 < (GREG ? R2 : 1); ++k2)
     g[k2] = (GREG && (R1 == T || t < R1))
                 ? (k2 < R2 / 2 ? gc[(t + R1 * k2) * W::GR] : gc[(L - R1 * k2 - t) * W::GR])
                 : make_float2(0.f, 0.f);
+  // the exchange area overlays the Green tile: every compute warp has its values before any writes
+  if constexpr (GREG) asm volatile("bar.sync 1, %0;\n" ::"r"(NW * 32) : "memory");
 #pragma unroll 1
   for (int iv = 0; iv < nact; ++iv) {
-    const int buf = iv & 1;
+    const int buf = iv % NS;
     const int slot = s_list[iv];
-    const bool ok = mbar_wait_abort(&full[buf], (unsigned)(iv >> 1) & 1u, &s_abort);
+    const bool ok = mbar_wait_abort(&full[buf], (unsigned)(iv / NS) & 1u, &s_abort);
     if (!__all_sync(0xffffffffu, ok)) break;
     count_run(a.sel);
     unsigned char* sb = reinterpret_cast<unsigned char*>(stage + (size_t)buf * NZ * P);
