@@ -570,7 +570,7 @@ struct ZW {
   static constexpr int GR = P + CPW;                                          // Ghat row [kz][GR], kz folded to [0, NZ]
   static constexpr int XP = pitch(imax(R1 * (R2 + 1), R2 * (R1 + 1)));        // exchange, padded rows
   static constexpr int TWA = R1 + 2, TWB = R2 + 2;                            // twiddle rows (16-byte aligned)
-  static constexpr int NS = 3;                                                // view buffers (TMA pipeline depth)
+  static constexpr int NS = 4;                                                // view buffers (TMA pipeline depth)
   // each thread's Green values stay in registers across the view loop where they fit (R2 <= 16);
   // the Green tile is then dead once they are loaded, and the exchange area reuses it
   static constexpr bool GREG = R2 <= 16;
