@@ -568,7 +568,8 @@ struct ZW {
   // then fall on disjoint banks; the Ghat rows [kz][P + CPW] are conflict-free for the same reason
   static constexpr int pitch(int n) { return n + (((16 / CPW) - n % 16) % 16 + 16) % 16; }
   static constexpr int GR = P + CPW;                                          // Ghat row [kz][GR], kz folded to [0, NZ]
-  static constexpr int XP = pitch(imax(R1 * (R2 + 1), R2 * (R1 + 1)));        // exchange, padded rows
+  // exchange rows of R + 2 entries: a thread reads its row with 16-byte loads (two entries each)
+  static constexpr int XP = pitch(imax(R1 * (R2 + 2), R2 * (R1 + 2)));
   static constexpr int TWA = R1 + 2, TWB = R2 + 2;                            // twiddle rows (16-byte aligned)
   static constexpr int NS = 4;                                                // view buffers (TMA pipeline depth)
   // each thread's Green values stay in registers across the view loop where they fit (R2 <= 16);
@@ -607,6 +608,7 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   using W = ZW<L>;
   constexpr int R1 = W::R1, R2 = W::R2, P = W::P, NZ = W::NZ, CPW = W::CPW, T = W::T, NW = W::NW;
   static_assert(W::ok, "k_zw needs T | 32");
+  static_assert(R1 % 2 == 0 && R2 % 2 == 0 && W::XP % 2 == 0, "16-byte exchange reads need even rows");
   extern __shared__ __align__(16) unsigned char zw_raw[];
   const unsigned raw = smem_addr(zw_raw);
   unsigned char* base = zw_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -724,12 +726,16 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
         v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
       }
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) xc[k1 * (R2 + 1) + t] = v[k1];
+      for (int k1 = 0; k1 < R1; ++k1) xc[k1 * (R2 + 2) + t] = v[k1];
     }
     __syncwarp();
     if (R1 == T || t < R1) {
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) u[n2] = xc[t * (R2 + 1) + n2];
+      for (int i = 0; i < R2 / 2; ++i) {
+        const float4 q = *reinterpret_cast<const float4*>(xc + t * (R2 + 2) + 2 * i);
+        u[2 * i] = make_float2(q.x, q.y);
+        u[2 * i + 1] = make_float2(q.z, q.w);
+      }
       Dft<R2, -1>::run(u);
       if constexpr (GREG) {
         if (slot_adj(a.sel, slot)) {
@@ -757,13 +763,17 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
     __syncwarp();
     if (R1 == T || t < R1) {
 #pragma unroll
-      for (int j1 = 0; j1 < R2; ++j1) xc[j1 * (R1 + 1) + t] = u[j1];
+      for (int j1 = 0; j1 < R2; ++j1) xc[j1 * (R1 + 2) + t] = u[j1];
     }
     __syncwarp();
     if (R2 == T || t < R2) {
       float2 w[R1];
 #pragma unroll
-      for (int m2 = 0; m2 < R1; ++m2) w[m2] = xc[t * (R1 + 1) + m2];
+      for (int i = 0; i < R1 / 2; ++i) {
+        const float4 q = *reinterpret_cast<const float4*>(xc + t * (R1 + 2) + 2 * i);
+        w[2 * i] = make_float2(q.x, q.y);
+        w[2 * i + 1] = make_float2(q.z, q.w);
+      }
       Dft<R1, +1, R1, R1 / 2>::run(w);
       // outputs z = t + R2 j2 (j2 < R1/2: z < nz), in place
 #pragma unroll
