@@ -685,6 +685,78 @@ def run_fista_mode(args):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------------------------------- Fig. 3 bead
+def run_bead_mode(args):
+    """Forward solves of the Fig. 3 bead (homogeneous sphere of diameter 3 lambda, dn = 0.1 in a
+    background of index 1.3388, 9 lambda box) at h = lambda/8 (72^3, 144-point transforms) and
+    lambda/16 (144^3, 288-point transforms): one plane wave along z, and 16 views on the NA 0.8 cone,
+    each batch timed with CUDA events after warm-up (plane waves + batched BiCGStab + far field)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1910_13844_gb300 as ls
+
+    lam, eta_b, dn_bead = 0.532, 1.3388, 0.1
+    box, radius = 9 * lam, 1.5 * lam
+    kb = 2 * np.pi * eta_b / lam
+    out = {"mode": "bead", "workload": "Fig. 3 bead: sphere diameter 3 lambda, dn 0.1, eta_b 1.3388, 9 lambda box, "
+                                       "tol 1e-06"}
+    for n in (72, 144):
+        h = box / n
+        shape = (n, n, n)
+        plan = ls.Plan(shape, kb, h, tol=TOL)
+        dnd = torch.from_numpy(ph.sphere(shape, radius / h, dn_bead).astype(np.float32)).cuda()
+        f = torch.empty_like(dnd)
+        ls.ls_scattering_potential(dnd, eta_b, kb, f)
+        N = n ** 3
+        octant = 8 * (n + 1) ** 3
+        for Q in (1, 16):
+            kvec = np.array([[0.0, 0.0, kb]]) if Q == 1 else ph.cone_directions(Q, NA, eta_b) * kb
+            tune = plan.autotune(Q, f)
+            uin = plan.field(Q)
+            u = plan.field(Q)
+            far = plan.detector(Q)
+            stats = []
+
+            def solve():
+                ls.ls_plane_waves(plan.handle, kvec, uin)
+                code, st = ls.ls_forward(plan.handle, f, uin, u, far)
+                stats.append((code, st))
+
+            for _ in range(2):
+                solve()
+            torch.cuda.synchronize()
+            reps = 5
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                solve()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            ls.ls_profile(plan.handle, True)
+            solve()
+            torch.cuda.synchronize()
+            prof = ls.ls_profile(plan.handle, False)
+            z_ms, z_launches, _, z_active = prof["z"]
+            z_gbs = (64 * N * z_active + octant * z_launches) / (z_ms / 1e3) / 1e9 if z_ms else None
+            its = [s["iterations"] for _, st in stats[-reps:] for s in st]
+            out[f"{n}^3_{Q}_views"] = {
+                "solves_per_s": round(Q / (ms / 1e3), 2), "ms_per_batch": round(ms, 3),
+                "mean_iterations": float(np.mean(its)),
+                "worst_status": int(max(c for c, _ in stats)),
+                "z_pass_gbs": round(z_gbs, 1) if z_gbs else None,
+                "z_kernel": "k_z (cp.async staging)" if 2 * n in (144, 288) else "k_zw",
+                "autotune": {k: tune[k] for k in ("z_tma", "ix_prefetch", "fx_views_fastest", "check_every",
+                                                  "use_graphs")},
+            }
+        plan.close()
+        torch.cuda.empty_cache()
+    print(json.dumps(out))
+
+
 # ----------------------------------------------------------------------------- reference arm (the oracle)
 def run_reference(args):
     ws, rank, local = dist_env()
@@ -733,7 +805,11 @@ def main():
     ap.add_argument("--fista", action="store_true", help="FISTA/TV reconstruction benchmark instead")
     ap.add_argument("--fista-iters", type=int, default=200)
     ap.add_argument("--tau", type=float, default=1e-6)
+    ap.add_argument("--bead", action="store_true", help="Fig. 3 bead forward solves (72^3 and 144^3) instead")
     args = ap.parse_args()
+    if args.bead:
+        run_bead_mode(args)
+        return
     if args.fista:
         run_fista_mode(args)
         return
