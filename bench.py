@@ -505,7 +505,7 @@ def cufft_matvec_baseline(torch, ls, plan, f, x, y_ours, reps=3, chunk=10):
     return us, float(d.max())
 
 
-def run_serving(torch, ls, n_requests, load=0.8, seed=2026, calib=12):
+def run_serving(torch, ls, n_requests, load=0.8, seed=2026, calib=12, iters_per_round=0):
     """Poisson arrivals at `load` x the measured batched capacity; returns latency and throughput.
 
     The comparison point is the same request mix solved one view per call (the same kernels without
@@ -549,7 +549,7 @@ def run_serving(torch, ls, n_requests, load=0.8, seed=2026, calib=12):
     reqs = serve_requests(n_requests + calib, seed)
     for r in reqs:   # every phantom is built on the host before any timing
         potential_for(r["shape"], r["seed"])
-    srv = ls.Server(kb, ph.VOXEL_UM, tol=TOL)
+    srv = ls.Server(kb, ph.VOXEL_UM, tol=TOL, iters_per_round=iters_per_round)
     for shape in SERVE_GRIDS:   # build the lanes (plans) before measuring
         w = {"shape": shape, "views": 8, "grad": True, "seed": 0}
         srv.wait(submit(srv, w, make(w)))
@@ -607,7 +607,8 @@ def run_serving(torch, ls, n_requests, load=0.8, seed=2026, calib=12):
     t_base = sum(r["views"] * per[r["shape"]][1 if r["grad"] else 0] for r in stream)
     lat = np.array(lat)
     return {
-        "requests": n_requests, "load": load, "rate_rps": round(rate, 3), "capacity_rps": round(cap_rps, 3),
+        "requests": n_requests, "load": load, "iters_per_round": iters_per_round or 2,
+        "rate_rps": round(rate, 3), "capacity_rps": round(cap_rps, 3),
         "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
         "mean_ms": round(float(lat.mean()), 2), "solves_per_s": round(total_solves / wall, 2),
         "one_view_at_a_time_solves_per_s": round(total_solves / t_base, 2),
@@ -627,7 +628,7 @@ def run_serve_mode(args):
 
     out = {"mode": "serve", "metric": METRIC}
     for load in args.loads:
-        out[f"load_{load}"] = run_serving(torch, ls, args.requests, load=load)
+        out[f"load_{load}"] = run_serving(torch, ls, args.requests, load=load, iters_per_round=args.iters_per_round)
     print(json.dumps(out))
 
 
@@ -802,6 +803,7 @@ def main():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 1.0])
     ap.add_argument("--serve-requests-in-step-line", type=int, default=60)
+    ap.add_argument("--iters-per-round", type=int, default=0, help="serving: iterations per lane round (0 = 2)")
     ap.add_argument("--fista", action="store_true", help="FISTA/TV reconstruction benchmark instead")
     ap.add_argument("--fista-iters", type=int, default=200)
     ap.add_argument("--tau", type=float, default=1e-6)

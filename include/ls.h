@@ -265,6 +265,7 @@ typedef struct {
   double tol;                /* solver tolerance (0 = 1e-6)                                                     */
   int max_iter;              /* 0 = 1000                                                                        */
   double k_b, voxel;         /* optics shared by all requests (1/um, um)                                        */
+  int iters_per_round;       /* BiCGStab iterations a lane runs between reads of its slot states (0 = 2)       */
 } ls_server_options;
 
 typedef struct {

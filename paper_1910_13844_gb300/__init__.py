@@ -376,9 +376,9 @@ class Server:
     """
 
     def __init__(self, k_b: float, voxel: float, tol: float = 1e-6, max_iter: int = 1000,
-                 hbm_budget_bytes: int = 0, max_views_per_grid: int = 0):
+                 hbm_budget_bytes: int = 0, max_views_per_grid: int = 0, iters_per_round: int = 0):
         opt = ls_server_options(hbm_budget_bytes=hbm_budget_bytes, max_views_per_grid=max_views_per_grid,
-                                tol=tol, max_iter=max_iter, k_b=k_b, voxel=voxel)
+                                tol=tol, max_iter=max_iter, k_b=k_b, voxel=voxel, iters_per_round=iters_per_round)
         self.handle = ls_server_create(opt)
         self._keep = {}
 

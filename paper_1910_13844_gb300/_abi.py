@@ -43,7 +43,7 @@ class ls_stats(C.Structure):
 
 class ls_server_options(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_views_per_grid", C.c_int), ("tol", C.c_double),
-                ("max_iter", C.c_int), ("k_b", C.c_double), ("voxel", C.c_double)]
+                ("max_iter", C.c_int), ("k_b", C.c_double), ("voxel", C.c_double), ("iters_per_round", C.c_int)]
 
 
 class ls_request(C.Structure):

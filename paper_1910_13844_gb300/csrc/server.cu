@@ -66,7 +66,7 @@ struct Lane {
 };
 
 constexpr int kResidBlocks = 32;   // residual partial blocks per view
-constexpr int kChunk = 4;          // BiCGStab iterations per round
+constexpr int kChunkDefault = 2;   // BiCGStab iterations per round unless the options say otherwise
 
 size_t plan_bytes(const ls_grid& g, int cap) {
   const size_t N = (size_t)g.nx * g.ny * g.nz;
@@ -384,8 +384,9 @@ struct ls_server {
     if (hi > lo) {
       ls_plan v = plan_slot_view(P, lo);
       if (l->n_resid > 0) seq_resid(&v, hi - lo, st);
+      const int chunk = opt.iters_per_round > 0 ? opt.iters_per_round : kChunkDefault;
       if (l->n_iter > 0 || l->n_resid > 0)
-        for (int k = 0; k < kChunk; ++k) seq_iter(&v, hi - lo, st);
+        for (int k = 0; k < chunk; ++k) seq_iter(&v, hi - lo, st);
       cudaMemcpyAsync(e.slots_h + lo, e.slots_d + lo, (size_t)(hi - lo) * sizeof(SlotDev), cudaMemcpyDeviceToHost, st);
     }
     cudaEventRecord(l->ev, st);
