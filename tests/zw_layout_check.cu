@@ -1,0 +1,53 @@
+// Host-side check of the shared-memory layout of the TMA-staged z pass (compiled by
+// tests/test_zw_layout.py; only compile-time constants are read, nothing runs on a GPU).
+#include <cstdio>
+#include "passes.cuh"
+using namespace lsgpu;
+
+static int failures = 0;
+#define REQUIRE(cond, L)                                               \
+  do {                                                                 \
+    if (!(cond)) {                                                     \
+      printf("L=%d: %s fails\n", L, #cond);                            \
+      ++failures;                                                      \
+    }                                                                  \
+  } while (0)
+
+template <int L>
+void check() {
+  using W = ZW<L>;
+  if (!W::ok) return;
+  // static shared memory of the kernel: the active-view list, the warp sums and the abort flag
+  constexpr size_t static_smem = kMaxLaunchSlots * sizeof(int) + 32 * sizeof(int) + 16;
+  constexpr size_t sm_capacity = 228 * 1024, per_cta_max = 227 * 1024, reserved_per_cta = 1024;
+  // every region starts on a 16-byte boundary (TMA tiles, 16-byte exchange and twiddle loads, mbarriers)
+  REQUIRE(W::stage_bytes % 1024 == 0, L);
+  REQUIRE(W::off_g % 16 == 0 && W::off_x % 16 == 0, L);
+  REQUIRE(W::off_twa % 16 == 0 && W::off_twb % 16 == 0 && W::off_bar % 16 == 0, L);
+  // the regions do not overlap, except the exchange area overlaying the Green tile when the Green
+  // values live in registers
+  REQUIRE(W::off_g >= (size_t)W::NS * W::stage_bytes, L);
+  REQUIRE(W::off_twa >= W::off_x + W::x_bytes, L);
+  REQUIRE(W::GREG ? W::off_twa >= W::off_g + W::g_bytes : W::off_x >= W::off_g + W::g_bytes, L);
+  REQUIRE(W::off_twb >= W::off_twa + (size_t)W::R2 * W::TWA * sizeof(float2), L);
+  REQUIRE(W::off_bar >= W::off_twb + (size_t)W::R1 * W::TWB * sizeof(float2), L);
+  REQUIRE(W::smem >= W::off_bar + 2 * W::NS * sizeof(uint64_t) + 1023, L);
+  // exchange rows: R1 rows of R2 + 2 and R2 rows of R1 + 2 entries fit a column's pitch, and the
+  // rows and pitch are even so that 16-byte reads stay aligned
+  REQUIRE(W::R1 * (W::R2 + 2) <= W::XP && W::R2 * (W::R1 + 2) <= W::XP, L);
+  REQUIRE(W::XP % 2 == 0 && W::R1 % 2 == 0 && W::R2 % 2 == 0, L);
+  REQUIRE((size_t)W::P * W::XP * sizeof(float2) <= W::x_bytes, L);
+  // twiddle rows read as float4 pairs
+  REQUIRE(W::TWA % 2 == 0 && W::TWB % 2 == 0, L);
+  // the resident CTAs the launch bounds ask for fit one SM
+  REQUIRE(W::smem <= per_cta_max, L);
+  REQUIRE((size_t)W::MINB * (W::smem + static_smem + reserved_per_cta) <= sm_capacity, L);
+  printf("L=%3d split %2dx%-2d NS=%d smem %6zu B x %d CTAs/SM\n", L, W::R1, W::R2, W::NS, W::smem, W::MINB);
+}
+
+int main() {
+  check<16>(); check<24>(); check<32>(); check<48>(); check<64>(); check<96>(); check<128>();
+  check<144>(); check<192>(); check<256>(); check<288>(); check<384>();
+  printf(failures ? "FAIL\n" : "OK\n");
+  return failures ? 1 : 0;
+}
