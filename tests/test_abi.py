@@ -68,3 +68,49 @@ def test_argument_errors_are_reported_without_touching_a_gpu(lib):
     assert b"pi" in L.ls_last_error()
     t = _abi.ls_tune()
     assert L.ls_autotune(None, 4, None, ctypes.byref(t), None) == _abi.LS_EINVAL
+
+
+def test_every_entry_point_rejects_bad_arguments_without_a_gpu(lib):
+    # each call below fails its argument check, which comes before any CUDA call
+    import ctypes as C
+
+    from paper_1910_13844_gb300 import _abi
+
+    L = _abi.load()
+    E = _abi.LS_EINVAL
+    g = _abi.ls_grid(16, 16, 16)
+    bad_grid = _abi.ls_grid(0, 16, 16)
+    one = (C.c_void_p * 1)(None)
+    k = (C.c_double * 3)(0.0, 0.0, 15.7)
+    assert L.ls_green_spectrum(None, 4, None, None) == E
+    assert L.ls_scattering_potential(None, 10, 1.333, 15.7, None, None) == E
+    assert L.ls_scattering_potential(None, 0, 1.333, 15.7, None, None) == _abi.LS_OK   # nothing to do
+    assert L.ls_plane_waves(None, 1, k, one, None) == E
+    assert L.ls_apply_green(None, None, None, 0, None) == E
+    assert L.ls_matvec(None, None, None, None, 0, None) == E
+    assert L.ls_matvec_noalloc(None, None, None, None, 0, None) == E
+    assert L.ls_matvec_batch(None, None, 1, one, one, 0, None) == E
+    assert L.ls_forward(None, None, 1, one, one, one, None, None) == E
+    assert L.ls_forward_warm(None, None, 1, one, one, one, one, None, None) == E
+    assert L.ls_farfield(None, None, 1, one, one, None) == E
+    assert L.ls_farfield_adjoint(None, 1, one, one, None) == E
+    assert L.ls_residual(0, 16, one, one, one, None, None) == E
+    assert L.ls_residual(1, 16, one, one, one, None, None) == E   # null view pointers
+    assert L.ls_gradient(None, None, 1, one, one, one, None, None, None, None) == E
+    assert L.ls_prox_tv(None, None, None, 0.1, 10, None, None) == E
+    assert L.ls_prox_tv(C.byref(bad_grid), None, None, 0.1, 10, None, None) == E
+    assert L.ls_prox_hs(C.byref(g), None, None, 0.1, 10, None, None) == E
+    assert L.ls_set_pupil(None, 1.0, 0.0) == E
+    assert L.ls_apply_pupil(None, 1, one, one, 0, None) == E
+    assert L.ls_incident_field(None, 1, one, k, one, None) == E
+    assert L.ls_profile(None, 1, None) == E
+    t = _abi.ls_tune()
+    assert L.ls_autotune(None, 1, None, C.byref(t), None) == E
+    srv = C.c_void_p()
+    opt = _abi.ls_server_options(k_b=15.7, voxel=0.25)   # k_b h > pi
+    assert L.ls_server_create(C.byref(opt), C.byref(srv)) == E
+    assert L.ls_server_create(None, C.byref(srv)) == E
+    ticket = C.c_uint64()
+    assert L.ls_submit(None, None, C.byref(ticket)) == E
+    assert L.ls_poll(None, 0, None) == E
+    assert L.ls_last_error()   # a message for the last failure
