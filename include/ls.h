@@ -73,7 +73,7 @@ typedef struct {
   int det_mx, det_my;  /* detector pixels (0 = nx, ny); m <= n and n - m even (centred window).     */
   double x_gamma;      /* detector plane position along z in micrometres; <= 0 means 3 L_z / 4.       */
   int max_restarts;    /* restarts from the true residual when it misses 10 tol at exit.  Default 4.  */
-  int check_every;     /* iterations between host reads of the convergence mask (0 = auto).          */
+  int check_every;     /* iterations between host reads of the convergence mask (0 = 2).             */
   int use_graphs;      /* 1 = replay the BiCGStab iteration from a captured CUDA graph.  Default 1.  */
 } ls_options;
 

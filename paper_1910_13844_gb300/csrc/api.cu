@@ -554,7 +554,7 @@ int engine_solve(ls_plan* P, int nslots, cudaStream_t st) {
     int rc = ensure_iter_graph(P, nslots);
     if (rc != LS_OK) return rc;
   }
-  const int chunk = P->opt.check_every > 0 ? P->opt.check_every : 4;
+  const int chunk = P->opt.check_every > 0 ? P->opt.check_every : 2;
   const long long max_rounds = (long long)P->opt.max_iter * (P->opt.max_restarts + 2) / chunk + 16;
   for (long long round = 0; round < max_rounds; ++round) {
     timed(P, LS_K_OTHER, nslots, st, [&] { launch_count(e.slots_d, nslots, e.counts_d, st); });

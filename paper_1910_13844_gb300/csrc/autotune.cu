@@ -134,7 +134,7 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   cur.z_tma = e.a2_map_ok ? 1 : 0;
   cur.ix_prefetch = 1;
   cur.fx_views_fastest = 1;
-  cur.check_every = P->opt.check_every > 0 ? P->opt.check_every : 4;
+  cur.check_every = P->opt.check_every > 0 ? P->opt.check_every : 2;
   cur.use_graphs = 1;
   cur.from_cache = 0;
   auto matvec = [&] { return tune_matvec(P, f, n_views, st); };
