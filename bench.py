@@ -36,8 +36,9 @@ METRIC = "LS matvec GB/s (%HBM) & solves/s at 128³×60 views; p50/p99 served so
 WORKLOADS = {
     "bench": dict(shape=(128, 128, 128), views=60, count=20, rmin=4.0, rmax=20.0, dn_max=0.05),
     "small": dict(shape=(32, 32, 32), views=4, count=4, rmin=2.0, rmax=6.0, dn_max=0.05),
-    # same grid and phantom as "bench" with 4 views: the case the full ncu captures run on
+    # same grid and phantom as "bench" with 4 and 16 views: the cases the full ncu captures run on
     "profile": dict(shape=(128, 128, 128), views=4, count=20, rmin=4.0, rmax=20.0, dn_max=0.05),
+    "profile16": dict(shape=(128, 128, 128), views=16, count=20, rmin=4.0, rmax=20.0, dn_max=0.05),
 }
 TOL = 1e-6
 NA = 0.8
@@ -124,6 +125,12 @@ Z_SOURCES = ["paper_1910_13844_gb300/csrc/passes.cuh", "paper_1910_13844_gb300/c
              "paper_1910_13844_gb300/csrc/common.cuh"]
 
 
+def opcodes_per_slot(kernel: str):
+    """ncu's FP32 opcode counts per slot for `kernel` (FADD2, FFMA, FMUL), if recorded for the current source."""
+    vals = {k: traffic_per_slot(kernel, f"{k}_per_slot") for k in ("fadd2", "ffma", "fmul")}
+    return vals if all(v is not None for v in vals.values()) else None
+
+
 def traffic_per_slot(kernel: str, field: str = "dram_bytes_per_slot"):
     """An ncu figure per slot for `kernel` (DRAM bytes, or FP32 pipe lane operations), if recorded for
     the current source (else None)."""
@@ -139,17 +146,26 @@ def traffic_per_slot(kernel: str, field: str = "dram_bytes_per_slot"):
     return float(rec[field])
 
 
-def alu_roofline(ops_per_view, launch_ms, views_per_launch, sm_mhz):
-    """The z pass against GB300's FP32 pipe (it performs ~8 flop per byte and is bound by FP32 issue,
-    not HBM): FP32 lane operations per view from ncu's opcode counts (FADD2 counted twice, FFMA and
-    FMUL once) over the live launch time; peak = 152 SMs x 128 FP32 lanes x the SM clock under load."""
-    if not ops_per_view or not launch_ms or not sm_mhz:
+def alu_roofline(opcodes, launch_ms, views_per_launch, fp32_peak, sm_count):
+    """The z pass against the FP32 pipe, with a measured denominator.
+
+    opcodes: ncu's warp-level counts per view of the pass's FP32 instructions (FADD2, FFMA, FMUL);
+    fp32_peak: lane operations per second of each kind measured on this GPU by ls_fp32_peak.  The
+    pipe's time floor for one view is sum_op lanes(op) x count(op) / rate(op) (a packed FADD2 is 64
+    lane operations); achieved = lane operations / live launch time, peak = lane operations / floor."""
+    if not opcodes or not launch_ms or not fp32_peak:
         return None
-    achieved = ops_per_view * views_per_launch / (launch_ms / 1e3) / 1e12
-    peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+    lanes = {"fadd2": 64.0, "ffma": 32.0, "fmul": 32.0}
+    ops = sum(lanes[k] * opcodes[k] for k in lanes)
+    floor_s = sum(lanes[k] * opcodes[k] / fp32_peak[k] for k in lanes)
+    achieved = ops * views_per_launch / (launch_ms / 1e3) / 1e12
+    peak = ops / floor_s / 1e12
     return {"kernel": "k_zw", "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2),
-            "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4),
-            "ops_per_view": int(ops_per_view), "peak_source": "152 SMs x 128 FP32 lanes x median SM clock"}
+            "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4), "ops_per_view": int(ops),
+            "peak_source": "measured: ls_fp32_peak (FFMA, FMUL, packed FADD2 microkernels) weighted by the "
+                           "pass's ncu opcode mix", "fp32_peak_lane_ops_per_s": {k: round(v / 1e12, 2) for k, v in
+                                                                                fp32_peak.items()},
+            "sm_count": sm_count}
 
 
 def dist_env():
@@ -175,13 +191,22 @@ class OracleView:
         self.k = ph.cone_directions(w["views"], NA, ph.ETA_B) * self.st.kb
         self.shape = shape
 
-    def solve(self, q, seconds_budget, iters_per_solve=None):
-        """Times the oracle's BiCGStab for view q at the bench tolerance, x0 = u_in.  A solve expected to
-        take longer than the budget is cut after the iterations that fit it and scaled by
-        iters_per_solve; otherwise it runs to convergence and is timed whole."""
+    def rhs(self, q, adjoint):
+        """Right-hand side of view q (untimed): the incident plane wave (forward), or G~^H r for a
+        seeded detector residual r (adjoint system of Alg. 1 line 6)."""
+        uin = self.model.plane_wave(self.shape, self.st.h, self.k[q % len(self.k)])
+        if not adjoint:
+            return uin
+        r = ph.complex_normal(self.st.det, seed=ph.SEED_NOISE + q)
+        return self.op.farfield_adjoint_fft(r)
+
+    def solve(self, q, seconds_budget, iters_per_solve=None, adjoint=False, b=None):
+        """Times the oracle's BiCGStab for view q at the bench tolerance, x0 = b (the forward system, or
+        the adjoint one).  A solve expected to take longer than the budget is cut after the iterations
+        that fit it and scaled by iters_per_solve; otherwise it runs to convergence and is timed whole."""
         model = self.model
-        uin = model.plane_wave(self.shape, self.st.h, self.k[q % len(self.k)])
-        A = lambda x: self.op.A(x, self.f)  # noqa: E731
+        uin = self.rhs(q, adjoint) if b is None else b
+        A = lambda x: self.op.A(x, self.f, adjoint=adjoint)  # noqa: E731
         t1 = time.perf_counter()
         A(uin)
         t1 = time.perf_counter() - t1
@@ -313,6 +338,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     iso = ls.ls_profile(plan.handle, False)
     cufft_us, cufft_diff = cufft_matvec_baseline(torch, ls, plan, f0, uin, u) if rank == 0 else (None, None)
+    fp32_peak = ls.ls_fp32_peak()
 
     solves_per_step = 2 * Q
     ms_step = ms_total / args.steps
@@ -395,8 +421,8 @@ def run_gpu(args):
             "algorithmic_bytes_per_launch": int(bytes_per_launch),
             "launch_ms": round(z_ms_launch, 4), "active_views_per_launch": round(active_per_launch, 2),
         },
-        "roofline_alu": alu_roofline(traffic_per_slot("z_pass", "fp32_lane_ops_per_slot"), z_ms_launch,
-                                     active_per_launch, clocks.summary().get("sm_mhz")),
+        "roofline_alu": alu_roofline(opcodes_per_slot("z_pass"), z_ms_launch, active_per_launch, fp32_peak,
+                                     torch.cuda.get_device_properties(dev).multi_processor_count),
         "matvec": {
             "gbs": round(mv_bytes / (mv_ms / 1e3) / 1e9, 1) if mv_ms else None,
             "frac_hbm": round(mv_bytes / (mv_ms / 1e3) / 1e9 / peak, 4) if mv_ms else None,
@@ -435,16 +461,23 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         out["serving"] = run_serving(torch, ls, args.serve_requests_in_step_line, load=0.8)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        ips = float(np.mean(stats_acc["fwd_iters"] + stats_acc["adj_iters"]))
-        cb = OracleView(w).solve(0, seconds_budget=20.0, iters_per_solve=ips)
-        how = (f"one full solve of view 0 to tol {TOL:g}: {cb['iterations']} iterations in {cb['seconds']:.1f} s"
-               if cb["full_solve"] else
-               f"{cb['iterations']} iterations of view 0 in {cb['seconds']:.1f} s, scaled by the GPU run's mean "
-               f"{ips:.1f} iterations per solve")
-        out["cpu_baseline"] = {"value": round(cb["solves_per_s"], 6), "unit": "solves/s", "cores": cb["threads"],
+        ov = OracleView(w)
+        cbs = []
+        for adj in (False, True):
+            ips = float(np.mean(stats_acc["adj_iters" if adj else "fwd_iters"]))
+            cbs.append(ov.solve(0, seconds_budget=15.0, iters_per_solve=ips, adjoint=adj, b=ov.rhs(0, adj)))
+        sps = 2.0 / sum(1.0 / c["solves_per_s"] for c in cbs)
+        how = "; ".join(
+            (f"{kind}: one full solve of view 0 to tol {TOL:g}, {c['iterations']} iterations in {c['seconds']:.1f} s"
+             if c["full_solve"] else
+             f"{kind}: {c['iterations']} iterations of view 0 in {c['seconds']:.1f} s, scaled to the GPU run's mean "
+             f"iterations per solve") for kind, c in zip(("forward", "adjoint"), cbs))
+        out["cpu_baseline"] = {"value": round(sps, 6), "unit": "solves/s", "cores": cbs[0]["threads"],
                                "kind": "oracle",
-                               "sample": f"FP64 oracle BiCGStab (x0 = u_in) on the same workload: {how}; "
-                                         f"oracle kernel build excluded"}
+                               "sample": f"FP64 oracle BiCGStab on the same workload, one forward solve (x0 = u_in) "
+                                         f"and one adjoint solve (x0 = G~^H r) of view 0, solves/s = 2 / total time "
+                                         f"(the GPU step is 60 forward + 60 adjoint solves): {how}; oracle kernel "
+                                         f"build and right-hand sides excluded"}
     if rank == 0:
         print(json.dumps(out))
     if plan is not None:
@@ -505,7 +538,7 @@ def cufft_matvec_baseline(torch, ls, plan, f, x, y_ours, reps=3, chunk=10):
     return us, float(d.max())
 
 
-def run_serving(torch, ls, n_requests, load=0.8, seed=2026, calib=12, iters_per_round=0):
+def run_serving(torch, ls, n_requests, load=0.8, seed=2026, calib=12, iters_per_round=0, baseline_views=16):
     """Poisson arrivals at `load` x the measured batched capacity; returns latency and throughput.
 
     The comparison point is the same request mix solved one view per call (the same kernels without
@@ -583,26 +616,32 @@ def run_serving(torch, ls, n_requests, load=0.8, seed=2026, calib=12, iters_per_
         _t.sleep(0.0005)
     wall = _t.perf_counter() - t0
     srv.close()
-    # one view per call, per grid: seconds per forward view and per forward+adjoint view
-    per = {}
+    # one view per call, per grid: seconds per forward view and per forward+adjoint view (median over
+    # `baseline_views` views, after one untimed forward + gradient that pays for the plan's workspace
+    # allocation, the iteration graph's capture and the kernels' first launches)
+    per, spread = {}, {}
     for shape in SERVE_GRIDS:
         plan = ls.Plan(shape, kb, ph.VOXEL_UM, tol=TOL)
-        r = {"shape": shape, "views": 4, "grad": True, "seed": 1}
+        r = {"shape": shape, "views": baseline_views, "grad": True, "seed": 1}
         b = make(r)
-        tf = tg = 0.0
-        for q in range(r["views"]):
+
+        def one(q):
             torch.cuda.synchronize()
             ts = _t.perf_counter()
             uin = plan.plane_waves(b["k"][q:q + 1])
             u, far, code, _ = plan.forward(b["f"], uin)
             torch.cuda.synchronize()
-            tf += _t.perf_counter() - ts
+            tf = _t.perf_counter() - ts
             res = torch.empty_like(far)
             ls.ls_residual(far, b["meas"][q:q + 1].contiguous(), res)
             plan.gradient(b["f"], res, u_fwd=u)
             torch.cuda.synchronize()
-            tg += _t.perf_counter() - ts
-        per[shape] = (tf / r["views"], tg / r["views"])
+            return tf, _t.perf_counter() - ts
+
+        one(0)   # warm-up, untimed
+        t = np.array([one(q) for q in range(r["views"])])
+        per[shape] = (float(np.median(t[:, 0])), float(np.median(t[:, 1])))
+        spread[shape] = [round(1e3 * float(np.percentile(t[:, k], p)), 2) for k in (0, 1) for p in (10, 90)]
         plan.close()
     t_base = sum(r["views"] * per[r["shape"]][1 if r["grad"] else 0] for r in stream)
     lat = np.array(lat)
@@ -613,8 +652,11 @@ def run_serving(torch, ls, n_requests, load=0.8, seed=2026, calib=12, iters_per_
         "mean_ms": round(float(lat.mean()), 2), "solves_per_s": round(total_solves / wall, 2),
         "one_view_at_a_time_solves_per_s": round(total_solves / t_base, 2),
         "one_view_ms_per_view": {f"{s[0]}^3": [round(1e3 * v[0], 2), round(1e3 * v[1], 2)] for s, v in per.items()},
+        "one_view_ms_p10_p90": {f"{s[0]}^3": v for s, v in spread.items()},
+        "batched_over_one_view": round(t_base / wall, 3),
         "mix": "grids {64,96,128,192}^3, 8-60 views, 70% forward / 30% gradient, dn <= 0.05, seed 2026; "
-               "one-view baseline: same mix at the per-grid one-view cost (forward, forward+adjoint)",
+               f"one-view baseline: same mix at the per-grid one-view cost (forward, forward+adjoint), median "
+               f"of {baseline_views} single-view calls per grid after one untimed warm-up call",
     }
 
 
@@ -766,17 +808,28 @@ def run_reference(args):
     w = WORKLOADS[args.workload]
     budget = 20.0
     ov = OracleView(w)                 # the oracle's kernel build, outside the timed steps
+
+    def step(q):
+        # one forward and one adjoint solve of view q (right-hand sides built outside the timing)
+        bf, ba = ov.rhs(q, False), ov.rhs(q, True)
+        f_ = ov.solve(q, seconds_budget=budget, b=bf)
+        a_ = ov.solve(q, seconds_budget=budget, adjoint=True, b=ba)
+        return {"seconds": f_["seconds"] + a_["seconds"], "iterations": f_["iterations"] + a_["iterations"],
+                "full_solve": f_["full_solve"] and a_["full_solve"],
+                "solves_per_s": 2.0 / (1.0 / f_["solves_per_s"] + 1.0 / a_["solves_per_s"]), "threads": f_["threads"]}
+
     for q in range(args.warmup):
-        ov.solve(q, seconds_budget=budget)
-    samples = [ov.solve(args.warmup + q, seconds_budget=budget) for q in range(args.steps)]
+        step(q)
+    samples = [step(args.warmup + q) for q in range(args.steps)]
     sps = float(np.median([s["solves_per_s"] for s in samples]))
     s0 = samples[0]
     full = all(s["full_solve"] for s in samples)
-    how = ("each step: one forward view solved to convergence by the FP64 oracle's BiCGStab (x0 = u_in, "
-           f"tol {TOL:g}; {np.mean([s['iterations'] for s in samples]):.1f} iterations on average); median over steps"
+    how = ("each step: one forward solve (x0 = u_in) and one adjoint solve (x0 = G~^H r) of one view, each to "
+           f"convergence by the FP64 oracle's BiCGStab (tol {TOL:g}; {np.mean([s['iterations'] for s in samples]):.1f} "
+           "iterations per step on average), solves/s = 2 / step time; median over steps"
            if full else
-           "each step: a bounded number of FP64 oracle BiCGStab iterations on one view, scaled to 8 iterations "
-           "per solve; median over steps")
+           "each step: a bounded number of FP64 oracle BiCGStab iterations of one forward and one adjoint solve, "
+           "scaled to 8 iterations per solve; median over steps")
     out = {
         "metric": METRIC, "value": round(sps, 6), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.median([s["seconds"] for s in samples])), 1),
@@ -802,7 +855,8 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving benchmark (Poisson request stream) instead")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 1.0])
-    ap.add_argument("--serve-requests-in-step-line", type=int, default=60)
+    ap.add_argument("--serve-requests-in-step-line", type=int, default=2000,
+                    help="requests of the serving stream (0.8 load) added to the step line (0: none)")
     ap.add_argument("--iters-per-round", type=int, default=0, help="serving: iterations per lane round (0 = 2)")
     ap.add_argument("--fista", action="store_true", help="FISTA/TV reconstruction benchmark instead")
     ap.add_argument("--fista-iters", type=int, default=200)

@@ -154,14 +154,17 @@ int ls_matvec_batch(ls_plan* plan, const float* f, int n_views, const ls_c64* co
  * synchronisation of cudaMalloc/cudaFree.  ls_matvec may allocate the plan's
  * workspace on first use; this call allocates nothing.  Its FFT
  * intermediates live in one static device array of 64 MiB inside the library
- * (48 bytes per voxel: grids up to 1398101 voxels, e.g. 96^3 or 128x128x64);
- * every GPU that loads the library holds that array until the process exits.
- * Larger grids return LS_EINVAL with the sizes in ls_last_error().  The first
- * call on each device looks up the array's device address, so make that first
- * call before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU (different streams, or different host threads) race and
- * must be ordered by the caller.  Nothing has to be cleared between calls.
- * The paper has no counterpart to this entry point. */
+ * (48 bytes per voxel: grids up to 1398101 voxels, e.g. 96^3 or 128x128x64).
+ * The array is reserved on a device, and its device address looked up, by the
+ * first ls_plan_create on that device (which allocates anyway); it is then
+ * held until the process exits.  So create the plan before handing the rest of
+ * the device's memory to a pool; this call itself looks nothing up, loads
+ * nothing and allocates nothing, on its first use too.  It must run on the
+ * device the plan was created on (LS_EINVAL otherwise).  Larger grids return
+ * LS_EINVAL with the sizes in ls_last_error().  All calls share the one array:
+ * calls that overlap on the GPU (different streams, or different host
+ * threads) race and must be ordered by the caller.  Nothing has to be cleared
+ * between calls.  The paper has no counterpart to this entry point. */
 int ls_matvec_noalloc(const ls_plan* plan, const float* f, const ls_c64* x, ls_c64* y, int adjoint,
                       void* cuda_stream);
 
@@ -255,6 +258,13 @@ int ls_gradient(ls_plan* plan, const float* f, int n_views, const ls_c64* const*
                 const ls_c64* const* u_fwd, const ls_c64* const* residuals,
                 const double* view_weights, float* grad, ls_stats* stats, void* cuda_stream);
 
+/* <a[q], b[q]> = sum_i conj(a[q][i]) b[q][i] over `count` entries for each of n_views pairs: the inner
+ * product of BiCGStab's scalars (Sec. 2.2), evaluated the way the solver's kernels evaluate theirs
+ * (float32 products and per-thread partial sums, every sum across threads in float64, fixed order).
+ * out: host array of 2 * n_views doubles (re, im per view).  Synchronous on cuda_stream. */
+int ls_inner_products(int n_views, size_t count, const ls_c64* const* a, const ls_c64* const* b, double* out,
+                      void* cuda_stream);
+
 /* ---------------------------------------------------------------- serving */
 
 enum ls_request_kind { LS_REQ_FORWARD = 0, LS_REQ_GRADIENT = 1 };
@@ -324,6 +334,33 @@ typedef struct {
  * out (host, may be NULL) receives the totals so far (synchronises the plan's
  * pending events).  Adds no work to the kernels themselves. */
 int ls_profile(ls_plan* plan, int enable, ls_kernel_times* out);
+
+/* ---------------------------------------------------------------- failure injection (tests) */
+
+/* Test-only failure injection, for checking the library's failure paths without faulting a GPU (the
+ * paper has no counterpart).  Every kind is off by default; LS_INJECT_NONE clears them all. */
+enum ls_inject_kind {
+  LS_INJECT_NONE = 0,         /* plan: clear every injection of this plan and the allocation counter      */
+  LS_INJECT_ZERO_SHADOW = 1,  /* plan: view `value` gets a zero shadow residual at the start of each solve, */
+                              /*   so <rh, v> vanishes in its first iteration (a forced BiCGStab breakdown;  */
+                              /*   a restart from the true residual recovers it); value < 0 turns it off    */
+  LS_INJECT_MAX_ROUNDS = 2,   /* plan: a solve's host loop stops after `value` rounds of launches; views    */
+                              /*   still running report LS_TIMEOUT; value < 0 restores the normal bound     */
+  LS_INJECT_ALLOC_FAIL = 3,   /* process-wide (plan may be NULL): the next `value` solver-workspace         */
+                              /*   allocations (plans and server lanes) fail with LS_ENOMEM                  */
+  LS_INJECT_Z_STALL = 4       /* plan: value > 0: the TMA-staged z pass waits on a barrier that nothing     */
+                              /*   completes and gives up after `value` ns (every copy it issued is still    */
+                              /*   waited for, with the normal one-second bound); the solve returns          */
+                              /*   LS_ECUDA.  value = 0 turns it off                                         */
+};
+int ls_debug_inject(ls_plan* plan, int kind, long long value);
+
+/* Measured FP32 throughput of the current device, for the FP32-pipe roofline of the FFT passes (no
+ * counterpart in the paper): out[0] scalar FFMA, out[1] scalar FMUL, out[2] packed add.f32x2, each in
+ * float lane operations per second (a packed add counts two), from kernels of known operation counts
+ * (eight independent dependency chains per thread, eight 256-thread blocks per SM) timed with CUDA
+ * events.  out: host array of 3 doubles.  Synchronous on cuda_stream. */
+int ls_fp32_peak(double* out, void* cuda_stream);
 
 /* ---------------------------------------------------------------- misc */
 

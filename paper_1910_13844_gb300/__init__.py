@@ -17,8 +17,9 @@ import torch
 
 from . import _abi
 from ._abi import (LS_BREAKDOWN, LS_EAGAIN, LS_ECUDA, LS_EINVAL, LS_ENOMEM, LS_ENOTFOUND, LS_EUNSUPPORTED,
-                   LS_NOT_CONVERGED, LS_OK, LS_PENDING, LS_REQ_FORWARD, LS_REQ_GRADIENT, LS_TIMEOUT, ls_grid,
-                   ls_options, ls_request, ls_result, ls_server_options, ls_stats)
+                   LS_INJECT_ALLOC_FAIL, LS_INJECT_MAX_ROUNDS, LS_INJECT_NONE, LS_INJECT_Z_STALL,
+                   LS_INJECT_ZERO_SHADOW, LS_NOT_CONVERGED, LS_OK, LS_PENDING, LS_REQ_FORWARD, LS_REQ_GRADIENT,
+                   LS_TIMEOUT, ls_grid, ls_options, ls_request, ls_result, ls_server_options, ls_stats)
 
 _lib = _abi.load()
 
@@ -28,7 +29,8 @@ __all__ = [
     "ls_farfield_adjoint", "ls_residual", "ls_gradient", "ls_server_create", "ls_submit", "ls_poll",
     "ls_server_destroy", "ls_status_string", "ls_last_error", "ls_workspace_bytes", "ls_profile", "library_path",
     "ls_matvec_noalloc", "ls_matvec_batch", "Server", "ls_set_pupil", "ls_apply_pupil", "ls_incident_field",
-    "ls_forward_warm", "ls_prox_tv", "ls_prox_hs", "ls_autotune",
+    "ls_forward_warm", "ls_prox_tv", "ls_prox_hs", "ls_autotune", "ls_inner_products", "ls_debug_inject",
+    "ls_fp32_peak",
 ]
 
 _SOFT = (LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN, LS_TIMEOUT, LS_PENDING)
@@ -261,6 +263,31 @@ def ls_residual(pred, meas, res, stream=None):
     loss = (C.c_double * n)()
     _check(_lib.ls_residual(n, count, a_p, a_m, a_r, loss, _stream(stream)), "ls_residual")
     return np.array(loss[:], dtype=np.float64)
+
+
+def ls_inner_products(a, b, stream=None):
+    """<a[q], b[q]> = sum conj(a[q]) b[q] per view (complex128 numpy array), the solver's inner product."""
+    a_a, n = _views(a)
+    a_b, m = _views(b)
+    if n != m:
+        raise ValueError("a and b need the same number of views")
+    count = (a[0] if isinstance(a, (list, tuple)) else a[0]).numel()
+    out = (C.c_double * (2 * n))()
+    _check(_lib.ls_inner_products(n, count, a_a, a_b, out, _stream(stream)), "ls_inner_products")
+    v = np.array(out[:], dtype=np.float64)
+    return v[0::2] + 1j * v[1::2]
+
+
+def ls_fp32_peak(stream=None) -> dict:
+    """Measured FP32 lane operations per second of the current device: FFMA, FMUL, packed add.f32x2."""
+    out = (C.c_double * 3)()
+    _check(_lib.ls_fp32_peak(out, _stream(stream)), "ls_fp32_peak")
+    return {"ffma": out[0], "fmul": out[1], "fadd2": out[2]}
+
+
+def ls_debug_inject(plan, kind: int, value: int = 0) -> int:
+    """Test-only failure injection (LS_INJECT_* kinds of include/ls.h); plan may be None for ALLOC_FAIL."""
+    return _check(_lib.ls_debug_inject(plan, int(kind), int(value)), "ls_debug_inject")
 
 
 def ls_gradient(plan: int, f, residuals, grad, u_in=None, u_fwd=None, view_weights=None, stream=None):

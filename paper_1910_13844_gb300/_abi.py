@@ -19,6 +19,12 @@ LS_EAGAIN = 8
 LS_ENOTFOUND = 9
 LS_EUNSUPPORTED = 10
 
+LS_INJECT_NONE = 0
+LS_INJECT_ZERO_SHADOW = 1
+LS_INJECT_MAX_ROUNDS = 2
+LS_INJECT_ALLOC_FAIL = 3
+LS_INJECT_Z_STALL = 4
+
 LS_REQ_FORWARD = 0
 LS_REQ_GRADIENT = 1
 
@@ -109,6 +115,9 @@ SIGNATURES = {
     "ls_apply_pupil": (C.c_int, [_P, C.c_int, _PP, _PP, C.c_int, _P]),
     "ls_incident_field": (C.c_int, [_P, C.c_int, _PP, C.POINTER(C.c_double), _PP, _P]),
     "ls_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(ls_tune), _P]),
+    "ls_inner_products": (C.c_int, [C.c_int, C.c_size_t, _PP, _PP, C.POINTER(C.c_double), _P]),
+    "ls_debug_inject": (C.c_int, [_P, C.c_int, C.c_longlong]),
+    "ls_fp32_peak": (C.c_int, [C.POINTER(C.c_double), _P]),
 }
 
 _lib = None

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "engine.h"
@@ -140,6 +141,72 @@ static int max_parts(const ls_plan* P) {
   return std::max(ix_blocks, 512);
 }
 
+// Test-only failure injection: the next g_fail_allocs engine allocations fail (ls_debug_inject).
+static std::atomic<long long> g_fail_allocs{0};
+
+static bool injected_alloc_failure() {
+  long long n = g_fail_allocs.load();
+  while (n > 0)
+    if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return true;
+  return false;
+}
+
+// Allocates the per-slot arrays of a workspace for nslots slots into e (which must be empty).
+// On failure everything allocated so far is released and e is left empty.
+static int engine_alloc(ls_plan* P, Engine& e, int nslots) {
+  if (injected_alloc_failure()) {
+    set_last_error("workspace allocation for %d views failed (injected)", nslots);
+    return LS_ENOMEM;
+  }
+  const int cap = nslots;
+  e.cap = cap;
+  e.N = P->N;
+  e.a1_stride = (size_t)2 * P->nx * P->ny * P->nz;
+  e.a2_stride = (size_t)4 * P->nx * P->ny * P->nz;
+  e.maxparts = max_parts(P);
+  int rc = LS_OK;
+  auto dev = [&](void** p, size_t bytes) {
+    if (rc != LS_OK) return;
+    const cudaError_t err = cudaMalloc(p, bytes);
+    if (err != cudaSuccess) {
+      *p = nullptr;
+      set_last_error("workspace allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(err));
+      rc = err == cudaErrorMemoryAllocation ? LS_ENOMEM : LS_ECUDA;
+    }
+  };
+  auto host = [&](void** p, size_t bytes) {
+    if (rc != LS_OK) return;
+    const cudaError_t err = cudaMallocHost(p, bytes);
+    if (err != cudaSuccess) {
+      *p = nullptr;
+      set_last_error("pinned allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(err));
+      rc = err == cudaErrorMemoryAllocation ? LS_ENOMEM : LS_ECUDA;
+    }
+  };
+  dev((void**)&e.vec, (size_t)NVEC * cap * e.N * sizeof(float2));
+  dev((void**)&e.a1, (size_t)cap * e.a1_stride * sizeof(float2));
+  dev((void**)&e.a2, (size_t)cap * e.a2_stride * sizeof(float2));
+  dev((void**)&e.far, (size_t)cap * P->mx * P->my * sizeof(float2));
+  dev((void**)&e.partials, (size_t)cap * e.maxparts * 4 * sizeof(double));
+  dev((void**)&e.slots_d, (size_t)cap * sizeof(SlotDev));
+  host((void**)&e.slots_h, (size_t)cap * sizeof(SlotDev));
+  dev((void**)&e.counts_d, 8 * sizeof(int));
+  host((void**)&e.counts_h, 8 * sizeof(int));
+  dev((void**)&e.ptrs_d, (size_t)4 * cap * sizeof(void*));
+  dev((void**)&e.kvec_d, (size_t)3 * cap * sizeof(double));
+  dev((void**)&e.weights_d, (size_t)cap * sizeof(float));
+  if (rc == LS_OK && cudaMemset(e.counts_d, 0, 8 * sizeof(int)) != cudaSuccess) rc = LS_ECUDA;
+  if (rc == LS_OK && cudaMemset(e.slots_d, 0, (size_t)cap * sizeof(SlotDev)) != cudaSuccess) rc = LS_ECUDA;
+  if (rc != LS_OK) {
+    engine_release(e);
+    return rc;
+  }
+  memset(e.slots_h, 0, (size_t)cap * sizeof(SlotDev));
+  memset(e.counts_h, 0, 8 * sizeof(int));
+  e.a2_map_ok = encode_a2_map(P, e) ? 1 : 0;
+  return LS_OK;
+}
+
 int engine_reserve(ls_plan* P, int nslots) {
   Engine& e = P->eng;
   if (nslots > kMaxLaunchSlots) {
@@ -147,34 +214,14 @@ int engine_reserve(ls_plan* P, int nslots) {
     return LS_EINVAL;
   }
   if (nslots <= e.cap) return LS_OK;
-  // keep the slot-independent pieces; reallocate the per-slot arrays
-  Engine old = e;
-  e = Engine();
-  e.cap_stream = old.cap_stream;
-  old.cap_stream = nullptr;
-  engine_release(old);
-  const int cap = nslots;
-  e.cap = cap;
-  e.N = P->N;
-  e.a1_stride = (size_t)2 * P->nx * P->ny * P->nz;
-  e.a2_stride = (size_t)4 * P->nx * P->ny * P->nz;
-  e.maxparts = max_parts(P);
-  LS_CUDA_TRY(cudaMalloc(&e.vec, (size_t)NVEC * cap * e.N * sizeof(float2)));
-  LS_CUDA_TRY(cudaMalloc(&e.a1, (size_t)cap * e.a1_stride * sizeof(float2)));
-  LS_CUDA_TRY(cudaMalloc(&e.a2, (size_t)cap * e.a2_stride * sizeof(float2)));
-  LS_CUDA_TRY(cudaMalloc(&e.far, (size_t)cap * P->mx * P->my * sizeof(float2)));
-  LS_CUDA_TRY(cudaMalloc(&e.partials, (size_t)cap * e.maxparts * 4 * sizeof(double)));
-  LS_CUDA_TRY(cudaMalloc(&e.slots_d, (size_t)cap * sizeof(SlotDev)));
-  LS_CUDA_TRY(cudaMallocHost(&e.slots_h, (size_t)cap * sizeof(SlotDev)));
-  LS_CUDA_TRY(cudaMalloc(&e.counts_d, 8 * sizeof(int)));
-  LS_CUDA_TRY(cudaMallocHost(&e.counts_h, 8 * sizeof(int)));
-  LS_CUDA_TRY(cudaMemset(e.counts_d, 0, 8 * sizeof(int)));
-  e.a2_map_ok = encode_a2_map(P, e) ? 1 : 0;
-  LS_CUDA_TRY(cudaMalloc(&e.ptrs_d, (size_t)4 * cap * sizeof(void*)));
-  LS_CUDA_TRY(cudaMalloc(&e.kvec_d, (size_t)3 * cap * sizeof(double)));
-  LS_CUDA_TRY(cudaMalloc(&e.weights_d, (size_t)cap * sizeof(float)));
-  LS_CUDA_TRY(cudaMemset(e.slots_d, 0, (size_t)cap * sizeof(SlotDev)));
-  memset(e.slots_h, 0, (size_t)cap * sizeof(SlotDev));
+  // keep the slot-independent pieces; reallocate the per-slot arrays (the old ones are freed first,
+  // so that the new ones can use their memory)
+  cudaStream_t cs = e.cap_stream;
+  e.cap_stream = nullptr;
+  engine_release(e);
+  int rc = engine_alloc(P, e, nslots);
+  e.cap_stream = cs;
+  if (rc != LS_OK) return rc;
   if (!e.cap_stream) LS_CUDA_TRY(cudaStreamCreateWithFlags(&e.cap_stream, cudaStreamNonBlocking));
   return LS_OK;
 }
@@ -265,6 +312,8 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   z.twb = P->twb_z;
   z.zwa = P->zwa_z;
   z.zwb = P->zwb_z;
+  z.wait_ns = (unsigned long long)P->inj_z_wait_ns;
+  z.stall = P->inj_z_stall;
   timed(P, LS_K_Z, nslots, st, [&] { P->pz.z(z, nslots, st); });
   StridedParams iy = fy_base(P, counted(P, sel, LS_K_IY), e.a2, e.a2_stride, e.a1, e.a1_stride, P->nz);
   iy.src_plane = (size_t)2 * P->ny * 2 * P->nx;
@@ -308,6 +357,8 @@ void seq_resid(ls_plan* P, int nslots, cudaStream_t st) {
   ix.vstride = e.N;
   ix.partials = e.partials;
   matvec_core(P, sel, nslots, fx, ix, st);
+  if (P->inj_zero_shadow_view >= 0 && P->inj_zero_shadow_view < nslots)
+    launch_zero_shadow(e.slots_d, P->inj_zero_shadow_view, e.vptr(V_RH), e.N, st);
   ScalarParams sc{e.slots_d, SLOT_RESID, PH_RESID, e.partials, ix_blocks(P)};
   timed(P, LS_K_SCALAR, nslots, st, [&] { launch_scalar(sc, nslots, st); });
 }
@@ -454,7 +505,8 @@ void seq_far_adjoint(ls_plan* P, int nslots, const float2* const* r_dev_table, u
 int ensure_iter_graph(ls_plan* P, int nslots) {
   Engine& e = P->eng;
   // the captured launches carry the plan's launch variants: recapture when ls_autotune changed them
-  const int variant = P->tune_z_tma | P->tune_ix_prefetch << 1 | P->tune_fx_views_fastest << 2;
+  const int variant = P->tune_z_tma | P->tune_ix_prefetch << 1 | P->tune_fx_views_fastest << 2 |
+                      (P->inj_z_stall || P->inj_z_wait_ns ? 1 << 3 : 0);
   if (e.iter_graph && e.iter_graph_slots == nslots && e.iter_graph_variant == variant) return LS_OK;
   if (e.iter_graph) {
     cudaGraphExecDestroy(e.iter_graph);
@@ -549,13 +601,16 @@ int tune_forward(ls_plan* P, const float* f, int n, cudaStream_t st) {
 int engine_solve(ls_plan* P, int nslots, cudaStream_t st) {
   Engine& e = P->eng;
   LS_CUDA_TRY(cudaMemcpyAsync(e.slots_d, e.slots_h, (size_t)nslots * sizeof(SlotDev), cudaMemcpyHostToDevice, st));
+  // the z pass's error word (a TMA wait that gave up) covers this solve only
+  LS_CUDA_TRY(cudaMemsetAsync(e.counts_d + 4, 0, sizeof(int), st));
   const bool graphs = P->opt.use_graphs != 0 && !P->prof.on;
   if (graphs) {
     int rc = ensure_iter_graph(P, nslots);
     if (rc != LS_OK) return rc;
   }
   const int chunk = P->opt.check_every > 0 ? P->opt.check_every : 2;
-  const long long max_rounds = (long long)P->opt.max_iter * (P->opt.max_restarts + 2) / chunk + 16;
+  long long max_rounds = (long long)P->opt.max_iter * (P->opt.max_restarts + 2) / chunk + 16;
+  if (P->inj_max_rounds >= 0) max_rounds = std::min(max_rounds, P->inj_max_rounds);
   for (long long round = 0; round < max_rounds; ++round) {
     timed(P, LS_K_OTHER, nslots, st, [&] { launch_count(e.slots_d, nslots, e.counts_d, st); });
     LS_CUDA_TRY(cudaMemcpyAsync(e.counts_h, e.counts_d, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -779,6 +834,14 @@ int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel, c
   P->x_gamma = P->opt.x_gamma > 0 ? P->opt.x_gamma : 0.75 * P->nz * P->h;
   int rc = LS_OK;
   cudaError_t se = cudaSuccess;
+  if (cudaGetDevice(&P->device) != cudaSuccess) {
+    set_last_error("no current CUDA device");
+    delete P;
+    return LS_ECUDA;
+  }
+  // ls_matvec_noalloc's static scratch: its address is looked up (and its module loaded) here,
+  // while creating a plan allocates anyway, so that the no-allocation entry point never does
+  P->noalloc_rc = noalloc_setup(&P->noalloc_scratch);
   if (!pass_for_length(L[0], &P->px, &se) || se != cudaSuccess ||
       !pass_for_length(L[1], &P->py, &se) || se != cudaSuccess ||
       !pass_for_length(L[2], &P->pz, &se) || se != cudaSuccess) {
@@ -1122,6 +1185,44 @@ int ls_residual(int n_views, size_t count, const ls_c64* const* pred, const ls_c
   return LS_OK;
 }
 
+int ls_inner_products(int n_views, size_t count, const ls_c64* const* a, const ls_c64* const* b, double* out,
+                      void* stream) {
+  if (n_views < 1 || count == 0 || !out) { set_last_error("bad arguments"); return LS_EINVAL; }
+  int rc = check_views(n_views, (const void* const*)a, "a", false);
+  if (!rc) rc = check_views(n_views, (const void* const*)b, "b", false);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nb = (int)std::min<size_t>(64, (count + 255) / 256);
+  void** tab = nullptr;
+  double* part = nullptr;
+  LS_CUDA_TRY(cudaMallocAsync((void**)&tab, (size_t)2 * n_views * sizeof(void*), st));
+  LS_CUDA_TRY(cudaMallocAsync((void**)&part, (size_t)n_views * nb * 4 * sizeof(double), st));
+  std::vector<void*> h(2 * n_views);
+  for (int q = 0; q < n_views; ++q) {
+    h[q] = (void*)a[q];
+    h[n_views + q] = (void*)b[q];
+  }
+  LS_CUDA_TRY(cudaMemcpyAsync(tab, h.data(), h.size() * sizeof(void*), cudaMemcpyHostToDevice, st));
+  ResidualParams p{count, (const float2* const*)tab, (const float2* const*)(tab + n_views), nullptr, part};
+  launch_inner(p, nb, n_views, st);
+  LS_CUDA_TRY(cudaGetLastError());
+  std::vector<double> hp((size_t)n_views * nb * 4);
+  LS_CUDA_TRY(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaFreeAsync(tab, st));
+  LS_CUDA_TRY(cudaFreeAsync(part, st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int q = 0; q < n_views; ++q) {
+    double re = 0, im = 0;
+    for (int k = 0; k < nb; ++k) {
+      re += hp[((size_t)q * nb + k) * 4];
+      im += hp[((size_t)q * nb + k) * 4 + 1];
+    }
+    out[2 * q] = re;
+    out[2 * q + 1] = im;
+  }
+  return LS_OK;
+}
+
 int ls_gradient(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_in, const ls_c64* const* u_fwd,
                 const ls_c64* const* residuals, const double* view_weights, float* grad, ls_stats* stats,
                 void* stream) {
@@ -1179,6 +1280,39 @@ int ls_gradient(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_
   LS_CUDA_TRY(cudaStreamSynchronize(st));
   if (fwd_status != LS_OK) return fwd_status;
   return adj_status;
+}
+
+int ls_debug_inject(ls_plan* P, int kind, long long value) {
+  switch (kind) {
+    case LS_INJECT_NONE:
+      if (!P) { set_last_error("null plan"); return LS_EINVAL; }
+      P->inj_zero_shadow_view = -1;
+      P->inj_max_rounds = -1;
+      P->inj_z_stall = 0;
+      P->inj_z_wait_ns = 0;
+      g_fail_allocs.store(0);
+      return LS_OK;
+    case LS_INJECT_ZERO_SHADOW:
+      if (!P) { set_last_error("null plan"); return LS_EINVAL; }
+      P->inj_zero_shadow_view = value >= 0 && value < kMaxLaunchSlots ? (int)value : -1;
+      return LS_OK;
+    case LS_INJECT_MAX_ROUNDS:
+      if (!P) { set_last_error("null plan"); return LS_EINVAL; }
+      P->inj_max_rounds = value >= 0 ? value : -1;
+      return LS_OK;
+    case LS_INJECT_ALLOC_FAIL:
+      g_fail_allocs.store(value > 0 ? value : 0);
+      return LS_OK;
+    case LS_INJECT_Z_STALL:
+      if (!P) { set_last_error("null plan"); return LS_EINVAL; }
+      if (value < 0) { set_last_error("wait limit must be >= 0"); return LS_EINVAL; }
+      P->inj_z_stall = value > 0 ? 1 : 0;
+      P->inj_z_wait_ns = value;
+      return LS_OK;
+    default:
+      set_last_error("unknown injection kind %d", kind);
+      return LS_EINVAL;
+  }
 }
 
 }  // extern "C"

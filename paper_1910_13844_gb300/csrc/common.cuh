@@ -88,6 +88,7 @@ struct SlotDev {
   double tol;
   double2 rho, alpha, omega, beta;   // BiCGStab scalars (complex, float64)
   double bnorm2, rnorm2, true_rnorm2;
+  double rhnorm2;      // ||rh||^2 of the shadow residual (fixed from the last (re)start)
 };
 
 // ---------------------------------------------------------------- error handling (host)

@@ -76,6 +76,16 @@ struct ls_plan {
   int tune_z_tma = 1;           // TMA-staged z pass where available (else the cp.async-staged one)
   int tune_ix_prefetch = 1;     // IX asks L2 for its epilogue operands at kernel start
   int tune_fx_views_fastest = 0;  // FX grid with views fastest (else row blocks fastest)
+  // test-only failure injection (ls_debug_inject); the defaults inject nothing
+  int inj_zero_shadow_view = -1;  // this view's shadow residual is zeroed at the start of a solve
+  long long inj_max_rounds = -1;  // host rounds a solve may take (-1: the normal bound)
+  int inj_z_stall = 0;            // the TMA-staged z pass waits on a barrier nothing completes
+  long long inj_z_wait_ns = 0;    // per-view wait limit of the TMA-staged z pass (0: one second)
+  // ls_matvec_noalloc: device address of the library's static scratch array on this plan's device,
+  // looked up when the plan is created (null, with noalloc_rc set, if that failed)
+  int device = 0;
+  void* noalloc_scratch = nullptr;
+  int noalloc_rc = 0;
   lsgpu::Engine eng;
   lsgpu::Profiler prof;
 };
@@ -109,6 +119,10 @@ int tune_matvec(ls_plan* P, const float* f, int n, cudaStream_t st);
 int tune_forward(ls_plan* P, const float* f, int n, cudaStream_t st);
 // P y (adjoint: P^H y) for one detector field; scratch holds 4 my mx double2
 int apply_pupil_device(ls_plan* P, const float2* in, float2* out, int adjoint, double2* scratch, cudaStream_t st);
+
+// ls_matvec_noalloc set-up (noalloc.cu): the device address of the static scratch array on the
+// current device; loads the array's module (reserving the array) if that has not happened yet.
+int noalloc_setup(void** addr);
 
 // Launch wrapper: when profiling is on, bracket the launch with an event pair.
 cudaEvent_t prof_event(ls_plan* P);

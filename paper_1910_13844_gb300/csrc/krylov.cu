@@ -10,7 +10,7 @@
 //   x = x + alpha p + omega s;  r = s - omega t
 // The p/s updates run inside the first FFT pass and v/t inside the last one
 // (passes.cuh); this file holds the x/r update and the per-slot scalar logic.
-// Dot products: float32 per thread and per warp, float64 above the warp.
+// Dot products: float32 products and per-thread partial sums, float64 from the warp shuffles up.
 #include "krylov.cuh"
 #include "passes.cuh"
 
@@ -62,6 +62,9 @@ __device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
   return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 __device__ __forceinline__ bool zfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// Relative breakdown threshold of BiCGStab's two inner products (the paper gives none).
+constexpr double kBreakdownRel = 1e-30;
 
 // One block per slot: sums the partials of the preceding kernel in a fixed
 // order (float64), then thread 0 advances the slot's BiCGStab state.
@@ -115,6 +118,7 @@ __global__ void __launch_bounds__(256) k_scalar(ScalarParams a) {
       // (re)start: rh = r (written by the pass), rho = <r, r>, alpha = omega = 1
       sd.status = LS_OK;
       sd.rho = make_double2(s0, 0.0);
+      sd.rhnorm2 = s0;   // rh = r
       sd.alpha = make_double2(1.0, 0.0);
       sd.omega = make_double2(1.0, 0.0);
       sd.beta = make_double2(0.0, 0.0);
@@ -124,8 +128,10 @@ __global__ void __launch_bounds__(256) k_scalar(ScalarParams a) {
     } break;
     case PH_ALPHA: {
       const double2 rv = make_double2(s0, s1);   // <rh, v>
+      const double vv = s2;                      // ||v||^2
       sd.matvecs += 1;
-      if (!zfinite(rv) || (fabs(rv.x) + fabs(rv.y)) <= 1e-300) {
+      // breakdown when <rh, v> vanishes relative to ||rh|| ||v|| (or is not finite)
+      if (!zfinite(rv) || !(hypot(rv.x, rv.y) > kBreakdownRel * sqrt(sd.rhnorm2 * vv))) {
         sd.status = LS_BREAKDOWN;
         sd.alpha = make_double2(0.0, 0.0);
         sd.flags = (sd.flags & ~SLOT_ITER) | SLOT_RESID;
@@ -157,8 +163,8 @@ __global__ void __launch_bounds__(256) k_scalar(ScalarParams a) {
         break;
       }
       const double om = fabs(sd.omega.x) + fabs(sd.omega.y);
-      const double rh = fabs(rho_new.x) + fabs(rho_new.y);
-      if (om == 0.0 || rh <= 1e-300 || !zfinite(rho_new)) {
+      // breakdown when rho = <rh, r> vanishes relative to ||rh|| ||r|| (or is not finite), or omega = 0
+      if (om == 0.0 || !zfinite(rho_new) || !(hypot(rho_new.x, rho_new.y) > kBreakdownRel * sqrt(sd.rhnorm2 * rr))) {
         sd.status = LS_BREAKDOWN;
         sd.flags = (sd.flags & ~SLOT_ITER) | SLOT_RESID;
         break;
@@ -168,6 +174,15 @@ __global__ void __launch_bounds__(256) k_scalar(ScalarParams a) {
       sd.first = 0;
     } break;
   }
+}
+
+// Test-only failure injection: zero the shadow residual of one slot at its initial residual
+// evaluation, so that <rh, v> vanishes in the first iteration (a forced BiCGStab breakdown).
+__global__ void k_zero_shadow(const SlotDev* slots, int slot, float2* rh, size_t n) {
+  if (slots[slot].checks != 0 || !(slots[slot].flags & SLOT_RESID)) return;
+  float2* v = rh + (size_t)slot * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    v[i] = make_float2(0.f, 0.f);
 }
 
 // Count slots per flag so the host can decide what to run next.
@@ -300,12 +315,30 @@ __global__ void __launch_bounds__(256) k_residual(ResidualParams a) {
   block_sum_store<4>(acc, a.partials + ((size_t)q * gridDim.x + blockIdx.x) * 4);
 }
 
+// <a, b> = sum conj(a) b per view (the inner product of the solver's scalars): float32 products and
+// per-thread partial sums, float64 from the warp shuffles up (the solver kernels' reduction)
+__global__ void __launch_bounds__(256) k_inner(ResidualParams a) {
+  const int q = blockIdx.y;
+  const float2* x = a.pred[q];
+  const float2* y = a.meas[q];
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < a.count; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 d = cdotterm(__ldg(x + i), __ldg(y + i));
+    acc[0] += d.x;
+    acc[1] += d.y;
+  }
+  block_sum_store<4>(acc, a.partials + ((size_t)q * gridDim.x + blockIdx.x) * 4);
+}
+
 // ------------------------------------------------------------------ launchers
 void launch_update(const UpdParams& a, int nblocks, int nslots, cudaStream_t st) {
   k_update<<<dim3(nblocks, nslots), 256, 0, st>>>(a);
 }
 void launch_scalar(const ScalarParams& a, int nslots, cudaStream_t st) {
   k_scalar<<<nslots, 256, 0, st>>>(a);
+}
+void launch_zero_shadow(const SlotDev* slots, int slot, float2* rh, size_t n, cudaStream_t st) {
+  k_zero_shadow<<<256, 256, 0, st>>>(slots, slot, rh, n);
 }
 void launch_count(const SlotDev* slots, int nslots, int* out, cudaStream_t st) {
   k_count<<<1, 256, 0, st>>>(slots, nslots, out);
@@ -350,6 +383,9 @@ void launch_gradient(const GradParams& a, cudaStream_t st) {
   int blocks = (int)((a.n + 255) / 256);
   if (blocks > 4864) blocks = 4864;
   k_gradient<<<blocks, 256, 0, st>>>(a);
+}
+void launch_inner(const ResidualParams& a, int nblocks, int nviews, cudaStream_t st) {
+  k_inner<<<dim3(nblocks, nviews), 256, 0, st>>>(a);
 }
 void launch_residual(const ResidualParams& a, int nblocks, int nviews, cudaStream_t st) {
   k_residual<<<dim3(nblocks, nviews), 256, 0, st>>>(a);

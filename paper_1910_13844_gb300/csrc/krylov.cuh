@@ -68,6 +68,8 @@ struct ResidualParams {
 void launch_update(const UpdParams& a, int nblocks, int nslots, cudaStream_t st);
 void launch_scalar(const ScalarParams& a, int nslots, cudaStream_t st);
 void launch_count(const SlotDev* slots, int nslots, int* out, cudaStream_t st);
+void launch_zero_shadow(const SlotDev* slots, int slot, float2* rh, size_t n, cudaStream_t st);
+void launch_inner(const ResidualParams& a, int nblocks, int nviews, cudaStream_t st);
 cudaError_t launch_plane_waves(const PlaneWaveParams& a, int nviews, cudaStream_t st);
 void launch_potential(const float* dn, size_t count, double eta_b, double kb, float* f, cudaStream_t st);
 void launch_far_reduce(const FarParams& a, int nslots, cudaStream_t st);

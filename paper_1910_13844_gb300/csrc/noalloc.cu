@@ -7,10 +7,16 @@
 // to its own pool at start-up, or a latency-bound loop in which a cudaMalloc
 // or cudaFree (both may synchronise the device) would stall other work.  This
 // entry point uses instead one static device array that is part of the
-// library image; every GPU that loads the library holds it until the process
-// exits.
-#include <mutex>
-
+// library image; every GPU that loads the library's module for it holds it
+// until the process exits.
+//
+// With lazy module loading the array is only reserved when its module is
+// first touched.  ls_plan_create does that (noalloc_setup below, on the
+// plan's device, while it allocates its own memory anyway) and keeps the
+// array's device address in the plan, so this call neither loads a module nor
+// looks anything up.  A plan belongs to the CUDA context it was created in;
+// after a context is destroyed (cudaDeviceReset), plans from before are
+// invalid and a new plan repeats the set-up.
 #include "engine.h"
 
 using namespace lsgpu;
@@ -22,30 +28,25 @@ namespace {
 constexpr size_t kNoallocScratchBytes = size_t(64) << 20;
 static __device__ __align__(256) float2 g_noalloc_scratch[kNoallocScratchBytes / sizeof(float2)];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-float2* g_scratch_addr[kMaxDevices] = {};
+}  // namespace
 
-// Device address of the static scratch on the current device, looked up once
-// per device (the name g_noalloc_scratch is only a host-side stand-in).
-int scratch_on_current_device(float2** out) {
-  int dev = -1;
-  LS_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_last_error("device ordinal %d out of range for the static scratch table", dev);
-    return LS_EINVAL;
+namespace lsgpu {
+
+// Device address of the static scratch on the current device.  The name
+// g_noalloc_scratch is only a host-side stand-in for the array; the address a
+// kernel can use is the one the runtime reports for the current device.
+int noalloc_setup(void** addr) {
+  *addr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(addr, g_noalloc_scratch);
+  if (e != cudaSuccess) {
+    *addr = nullptr;
+    set_last_error("static scratch of ls_matvec_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LS_ENOMEM : LS_ECUDA;
   }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    LS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_scratch_addr[dev] = static_cast<float2*>(p);
-  }
-  *out = g_scratch_addr[dev];
   return LS_OK;
 }
 
-}  // namespace
+}  // namespace lsgpu
 
 extern "C" int ls_matvec_noalloc(const ls_plan* P, const float* f, const ls_c64* x, ls_c64* y, int adjoint,
                                  void* stream) {
@@ -62,11 +63,19 @@ extern "C" int ls_matvec_noalloc(const ls_plan* P, const float* f, const ls_c64*
                    kNoallocScratchBytes / 48);
     return LS_EINVAL;
   }
-  float2* scratch = nullptr;
-  int rc = scratch_on_current_device(&scratch);
-  if (rc != LS_OK) return rc;
-  float2* a1 = scratch;
-  float2* a2 = scratch + a1n;
+  if (!P->noalloc_scratch) {
+    set_last_error("ls_matvec_noalloc: the static scratch could not be set up when the plan was created (%s)",
+                   ls_status_string(P->noalloc_rc));
+    return P->noalloc_rc ? P->noalloc_rc : LS_ECUDA;
+  }
+  int dev = -1;
+  LS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != P->device) {
+    set_last_error("ls_matvec_noalloc: the current device is %d, the plan was created on device %d", dev, P->device);
+    return LS_EINVAL;
+  }
+  float2* a1 = static_cast<float2*>(P->noalloc_scratch);
+  float2* a2 = a1 + a1n;
   cudaStream_t st = (cudaStream_t)stream;
 
   // Every scratch element that a pass reads is written earlier in the same

@@ -81,6 +81,8 @@ struct ZParams {
   int use_tma;                 // tmap is valid: the TMA-staged z pass may run
   int slot0;                   // slot coordinate of this launch's slot 0 in tmap
   int* err;                    // set to 1 if a wait for a TMA copy gave up (the launch's output is invalid)
+  unsigned long long wait_ns = 0;   // limit of the TMA-staged pass's per-view waits (0: one second)
+  int stall = 0;               // test only: the compute warps' first wait is on a barrier nothing completes
 };
 
 struct IxParams {
@@ -183,13 +185,18 @@ struct Geo {
   static constexpr size_t smem_z = (size_t)(2 * L + L) * PS * sizeof(float2);   // exchange + Ghat + 2 staging halves
 };
 
-// Warp-then-block reduction of NV float partial sums; thread 0 writes doubles to out[0..NV).
+// Warp-then-block reduction of NV per-thread float partial sums; thread 0 writes doubles to
+// out[0..NV).  Each thread's partial is promoted to double before the first shuffle, so every sum
+// across threads (warp shuffles and the block level) is accumulated in float64.
 template <int NV>
-__device__ __forceinline__ void block_sum_store(float (&acc)[NV], double* out) {
+__device__ __forceinline__ void block_sum_store(const float (&acc)[NV], double* out) {
+  double d[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) d[j] = (double)acc[j];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-    for (int j = 0; j < NV; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+    for (int j = 0; j < NV; ++j) d[j] += __shfl_xor_sync(0xffffffffu, d[j], o);
   __shared__ double wsum[32][NV];
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
@@ -197,7 +204,7 @@ __device__ __forceinline__ void block_sum_store(float (&acc)[NV], double* out) {
   __syncthreads();
   if (lane == 0)
 #pragma unroll
-    for (int j = 0; j < NV; ++j) wsum[w][j] = (double)acc[j];
+    for (int j = 0; j < NV; ++j) wsum[w][j] = d[j];
   __syncthreads();
   if (w == 0) {
     double v[NV];
@@ -518,15 +525,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
 }
-// mbar_wait that also gives up as soon as another thread of the CTA has set *abort; a wait that
-// runs out sets *abort itself.
-__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, volatile int* abort) {
+// mbar_wait that also gives up as soon as another thread of the CTA has set *abort, or after
+// limit_ns; a wait that runs out sets *abort itself.
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, volatile int* abort,
+                                                unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (global_ns() - t0 > 1000000000ull) {
+    if (global_ns() - t0 > limit_ns) {
       *abort = 1;
       return false;
     }
@@ -584,7 +592,8 @@ struct ZW {
   static constexpr size_t off_twa = off_x + (GREG ? (g_bytes > x_bytes ? g_bytes : x_bytes) : x_bytes);
   static constexpr size_t off_twb = off_twa + r16((size_t)R2 * TWA * sizeof(float2));
   static constexpr size_t off_bar = off_twb + r16((size_t)R1 * TWB * sizeof(float2));
-  static constexpr size_t smem = off_bar + 2 * NS * sizeof(uint64_t) + 1024; // + room to align the base to 1024
+  static constexpr int NBAR = 2 * NS + 1;                                     // full[NS], done[NS], never
+  static constexpr size_t smem = off_bar + NBAR * sizeof(uint64_t) + 1024;    // + room to align the base to 1024
 };
 
 // Byte offset of element (z, c) of a [NZ][16] complex64 tile written by TMA with the 128-byte swizzle
@@ -620,6 +629,7 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   constexpr int NS = W::NS;
   uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);   // [NS]: a view's tile has landed
   uint64_t* done = full + NS;                                         // [NS]: the compute warps are done with it
+  uint64_t* never = done + NS;                                        // no thread arrives on it (stall test)
   __shared__ int s_list[kMaxLaunchSlots];
   __shared__ int s_ws[32];
   __shared__ int s_abort;
@@ -632,12 +642,14 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   const int ky = blockIdx.x / tiles_c;
   const int kx0 = (blockIdx.x % tiles_c) * P;
   const bool producer = warp == NW;
+  const unsigned long long limit_ns = a.wait_ns ? a.wait_ns : 1000000000ull;
   if (producer && lane == 0) {
     s_abort = 0;
     for (int k = 0; k < NS; ++k) {
       mbar_init(&full[k], 1);
       mbar_init(&done[k], NW);
     }
+    mbar_init(never, 1);
     mbar_init_fence();
     for (int k = 0; k < NS && k < nact; ++k) {
       mbar_expect_tx(&full[k], (unsigned)W::stage_bytes);
@@ -663,7 +675,7 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
     int iv = 0;
     for (; iv < nact; ++iv) {
       const int buf = iv % NS;
-      if (!mbar_wait_abort(&done[buf], (unsigned)(iv / NS) & 1u, &s_abort)) break;
+      if (!mbar_wait_abort(&done[buf], (unsigned)(iv / NS) & 1u, &s_abort, limit_ns)) break;
       float2* sb = stage + (size_t)buf * NZ * P;
       tma_store_4d(&a.tmap, sb, 2 * kx0, ky, 0, a.slot0 + s_list[iv]);
       bulk_commit();
@@ -676,7 +688,8 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
     bulk_wait_read_all();
     if (iv < nact) {
       // gave up at view iv: flag it, and give the loads still in flight into this CTA's buffers
-      // (views iv .. iv + NS - 1, all issued) a bounded time to land
+      // (views iv .. iv + NS - 1, all issued) a bounded time to land (one second each, whatever
+      // the per-view limit)
       atomicExch(a.err, 1);
       for (int j = iv; j < iv + NS && j < nact; ++j) mbar_wait(&full[j % NS], (unsigned)(j / NS) & 1u);
     }
@@ -704,7 +717,8 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   for (int iv = 0; iv < nact; ++iv) {
     const int buf = iv % NS;
     const int slot = s_list[iv];
-    const bool ok = mbar_wait_abort(&full[buf], (unsigned)(iv / NS) & 1u, &s_abort);
+    const bool ok = (a.stall && iv == 0) ? mbar_wait_abort(never, 0u, &s_abort, limit_ns)
+                                         : mbar_wait_abort(&full[buf], (unsigned)(iv / NS) & 1u, &s_abort, limit_ns);
     if (!__all_sync(0xffffffffu, ok)) break;
     count_run(a.sel);
     unsigned char* sb = reinterpret_cast<unsigned char*>(stage + (size_t)buf * NZ * P);
@@ -853,6 +867,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
           a.out0[i] = vv;
           float2 d = cdotterm(__ldg(a.in1 + i), vv);   // conj(rh) v
           acc[0] += d.x; acc[1] += d.y;
+          acc[2] += vv.x * vv.x + vv.y * vv.y;          // ||v||^2 (relative breakdown test)
         } break;
         case IX_BICG_T: {
           float2 ss = __ldg(a.in0 + i);

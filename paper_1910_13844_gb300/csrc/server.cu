@@ -237,6 +237,12 @@ struct ls_server {
 
   void fail(Request* r, int code) {
     r->status = code;
+    if (r->lane && r->s0 >= 0) {
+      // its slots stop iterating (they may lie inside the range the lane's next rounds launch over)
+      Engine& e = r->lane->plan->eng;
+      for (int q = 0; q < r->n; ++q) e.slots_h[r->s0 + q].flags = 0;
+      upload_slots(r->lane, r->s0, r->n);
+    }
     release(r);
   }
 
@@ -388,6 +394,8 @@ struct ls_server {
       if (l->n_iter > 0 || l->n_resid > 0)
         for (int k = 0; k < chunk; ++k) seq_iter(&v, hi - lo, st);
       cudaMemcpyAsync(e.slots_h + lo, e.slots_d + lo, (size_t)(hi - lo) * sizeof(SlotDev), cudaMemcpyDeviceToHost, st);
+      // the z pass's error word (a TMA wait that gave up), read back with the slot states
+      cudaMemcpyAsync(e.counts_h + 4, e.counts_d + 4, sizeof(int), cudaMemcpyDeviceToHost, st);
     }
     cudaEventRecord(l->ev, st);
     l->issued = true;
@@ -398,6 +406,13 @@ struct ls_server {
     l->issued = false;
     Engine& e = l->plan->eng;
     if (err == cudaSuccess) err = cudaGetLastError();
+    bool zfail = false;
+    if (e.counts_h[4]) {
+      // a round's z pass gave up on a copy: the round's results are invalid for every request in it
+      zfail = true;
+      e.counts_h[4] = 0;
+      cudaMemsetAsync(e.counts_d + 4, 0, sizeof(int), l->stream);
+    }
     l->n_iter = l->n_resid = 0;
     std::vector<Request*> seen;
     for (int s = 0; s < l->cap; ++s) {
@@ -407,7 +422,7 @@ struct ls_server {
       seen.push_back(r);
     }
     for (Request* r : seen) {
-      if (err != cudaSuccess) { fail(r, LS_ECUDA); continue; }
+      if (err != cudaSuccess || zfail) { fail(r, LS_ECUDA); continue; }
       if (r->phase == PH_FINISHING) {
         release(r);
         continue;

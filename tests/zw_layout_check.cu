@@ -31,7 +31,7 @@ void check() {
   REQUIRE(W::GREG ? W::off_twa >= W::off_g + W::g_bytes : W::off_x >= W::off_g + W::g_bytes, L);
   REQUIRE(W::off_twb >= W::off_twa + (size_t)W::R2 * W::TWA * sizeof(float2), L);
   REQUIRE(W::off_bar >= W::off_twb + (size_t)W::R1 * W::TWB * sizeof(float2), L);
-  REQUIRE(W::smem >= W::off_bar + 2 * W::NS * sizeof(uint64_t) + 1023, L);
+  REQUIRE(W::NBAR == 2 * W::NS + 1 && W::smem >= W::off_bar + W::NBAR * sizeof(uint64_t) + 1023, L);
   // exchange rows: R1 rows of R2 + 2 and R2 rows of R1 + 2 entries fit a column's pitch, and the
   // rows and pitch are even so that 16-byte reads stay aligned
   REQUIRE(W::R1 * (W::R2 + 2) <= W::XP && W::R2 * (W::R1 + 2) <= W::XP, L);
