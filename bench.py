@@ -447,6 +447,7 @@ def run_gpu(args):
                    "crop, subtract; 10 views per batched transform; timed comparison only",
         },
         "update_gbs": update_gbs,
+        "fp32_peak_tlane_ops": {k: round(v / 1e12, 2) for k, v in fp32_peak.items()},
         "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in prof.items()} if total_kernel_ms else {},
         "dominant_kernel": dominant,
         "gpu_launches": launches,

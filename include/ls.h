@@ -75,6 +75,9 @@ typedef struct {
   int max_restarts;    /* restarts from the true residual when it misses 10 tol at exit.  Default 4.  */
   int check_every;     /* iterations between host reads of the convergence mask (0 = 2).             */
   int use_graphs;      /* 1 = replay the BiCGStab iteration from a captured CUDA graph.  Default 1.  */
+  double cone_sin_theta; /* built-in illumination (u_in == NULL): view q of n is the plane wave of wave   */
+                         /* vector k_b (s cos phi_q, s sin phi_q, sqrt(1 - s^2)), s = cone_sin_theta     */
+                         /* (= NA / eta_b), phi_q = 2 pi q / n (the cone of Fig. 1).  Default 0 (+z).    */
 } ls_options;
 
 typedef struct {
@@ -170,7 +173,9 @@ int ls_matvec_noalloc(const ls_plan* plan, const float* f, const ls_c64* x, ls_c
 
 /* Forward model for n_views illuminations of one potential f (eqs. lipp1, lipp2):
  * BiCGStab on (I - G diag f) u = u_in[q] from u = u_in[q], all views batched,
- * then the far field y_q = G~ (f .* u_q) on the detector.  u_out[q] (N) and
+ * then the far field y_q = G~ (f .* u_q) on the detector.  u_in == NULL: the
+ * plan's built-in plane waves (ls_options.cone_sin_theta), generated in the
+ * solver's workspace (no caller buffer, no copies).  u_out[q] (N) and
  * far[q] (my*mx) may each be NULL (u_out == NULL: fields not returned;
  * far == NULL: far field skipped).  stats: host array of n_views or NULL.
  * Returns LS_OK, LS_NOT_CONVERGED or LS_BREAKDOWN (worst view), or an error. */
@@ -251,8 +256,10 @@ int ls_residual(int n_views, size_t count, const ls_c64* const* pred, const ls_c
 /* Data-fidelity gradient (Alg. 1 line 6, Jacobian adjoint):
  *   grad = sum_q c_q Re(conj(u_q) .* w_q),  (I - G^H diag f) w_q = G~^H r_q,
  * with r_q = residuals[q] (my*mx, e.g. H_q(f) - y_q) and c_q = view_weights[q]
- * (host array; NULL means 1).  u_fwd[q] are the forward fields (checkpoint); if
- * u_fwd == NULL they are recomputed from u_in (u_in is ignored otherwise).
+ * (host array; NULL means 1; double where the paper's c_q = 1/||y_q||^2 can span
+ * many decades).  u_fwd[q] are the forward fields (checkpoint); if u_fwd == NULL
+ * they are recomputed from u_in (NULL: the built-in plane waves, as in
+ * ls_forward); u_in is ignored otherwise.
  * grad: N float32, overwritten.  stats: host array of n_views (adjoint solves) or NULL. */
 int ls_gradient(ls_plan* plan, const float* f, int n_views, const ls_c64* const* u_in,
                 const ls_c64* const* u_fwd, const ls_c64* const* residuals,

@@ -188,9 +188,13 @@ def ls_matvec_noalloc(plan: int, f, x, y, adjoint: bool = False, stream=None) ->
                   "ls_matvec_noalloc")
 
 
-def ls_forward(plan: int, f, u_in, u_out=None, far=None, stream=None):
-    """Returns (status, [stats dict per view])."""
+def ls_forward(plan: int, f, u_in, u_out=None, far=None, stream=None, n_views=None):
+    """Returns (status, [stats dict per view]).  u_in None: the plan's built-in plane waves for n_views views."""
     a_in, n = _views(u_in)
+    if u_in is None:
+        if not n_views:
+            raise ValueError("n_views is needed when u_in is None")
+        n = int(n_views)
     a_out, _ = _views(u_out)
     a_far, _ = _views(far)
     st = (ls_stats * n)()
@@ -378,11 +382,12 @@ class Plan:
         ls_plane_waves(self.handle, k, u, stream)
         return u
 
-    def forward(self, f, u_in, want_fields=True, want_far=True, stream=None):
-        q = u_in.shape[0]
+    def forward(self, f, u_in, want_fields=True, want_far=True, stream=None, n_views=None):
+        """u_in None: the built-in plane waves (options cone_sin_theta) for n_views views."""
+        q = u_in.shape[0] if u_in is not None else int(n_views)
         u = self.field(q) if want_fields else None
         far = self.detector(q) if want_far else None
-        code, stats = ls_forward(self.handle, f, u_in, u, far, stream)
+        code, stats = ls_forward(self.handle, f, u_in, u, far, stream, n_views=q)
         return u, far, code, stats
 
     def autotune(self, n_views: int, f, stream=None) -> dict:

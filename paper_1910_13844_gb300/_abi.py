@@ -36,7 +36,8 @@ class ls_grid(C.Structure):
 class ls_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("oversample_p", C.c_int),
                 ("det_mx", C.c_int), ("det_my", C.c_int), ("x_gamma", C.c_double),
-                ("max_restarts", C.c_int), ("check_every", C.c_int), ("use_graphs", C.c_int)]
+                ("max_restarts", C.c_int), ("check_every", C.c_int), ("use_graphs", C.c_int),
+                ("cone_sin_theta", C.c_double)]
 
 
 class ls_stats(C.Structure):

@@ -193,7 +193,7 @@ static int engine_alloc(ls_plan* P, Engine& e, int nslots) {
   dev((void**)&e.counts_d, 8 * sizeof(int));
   host((void**)&e.counts_h, 8 * sizeof(int));
   dev((void**)&e.ptrs_d, (size_t)4 * cap * sizeof(void*));
-  dev((void**)&e.kvec_d, (size_t)3 * cap * sizeof(double));
+  dev((void**)&e.kvec_d, (size_t)6 * cap * sizeof(double));   // 3 per view, twice (built-in plane waves)
   dev((void**)&e.weights_d, (size_t)cap * sizeof(float));
   if (rc == LS_OK && cudaMemset(e.counts_d, 0, 8 * sizeof(int)) != cudaSuccess) rc = LS_ECUDA;
   if (rc == LS_OK && cudaMemset(e.slots_d, 0, (size_t)cap * sizeof(SlotDev)) != cudaSuccess) rc = LS_ECUDA;
@@ -743,6 +743,7 @@ void ls_default_options(ls_options* opt) {
   opt->max_restarts = 4;
   opt->check_every = 0;
   opt->use_graphs = 1;
+  opt->cone_sin_theta = 0.0;
 }
 
 const char* ls_status_string(int status) {
@@ -822,6 +823,11 @@ int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel, c
   if (P->opt.max_iter <= 0) P->opt.max_iter = 1000;
   if (P->opt.oversample_p <= 0) P->opt.oversample_p = 4;
   if (P->opt.max_restarts < 0) P->opt.max_restarts = 0;
+  if (!(P->opt.cone_sin_theta >= 0.0 && P->opt.cone_sin_theta <= 1.0)) {
+    set_last_error("cone_sin_theta must lie in [0, 1]");
+    delete P;
+    return LS_EINVAL;
+  }
   P->mx = P->opt.det_mx > 0 ? P->opt.det_mx : P->nx;
   P->my = P->opt.det_my > 0 ? P->opt.det_my : P->ny;
   if (P->mx > P->nx || P->my > P->ny || ((P->nx - P->mx) & 1) || ((P->ny - P->my) & 1)) {
@@ -1041,15 +1047,55 @@ int ls_matvec_batch(ls_plan* P, const float* f, int n_views, const ls_c64* const
   return LS_OK;
 }
 
+// Wave vectors of the plan's built-in illumination for n views: a cone of half-angle theta around
+// +z (sin theta = opt.cone_sin_theta), azimuths 2 pi q / n (the set-up of Fig. 1).
+static void builtin_kvec(const ls_plan* P, int n, std::vector<double>& k) {
+  const double s = P->opt.cone_sin_theta, c = sqrt(std::max(0.0, 1.0 - s * s));
+  k.assign(3 * (size_t)n, 0.0);
+  for (int q = 0; q < n; ++q) {
+    const double phi = 2.0 * kPi * q / n;
+    k[3 * q] = P->kb * s * cos(phi);
+    k[3 * q + 1] = P->kb * s * sin(phi);
+    k[3 * q + 2] = P->kb * c;
+  }
+}
+
+// Built-in plane waves for slots [0, n), written straight into b and (unless initial guesses are
+// given) x0 = b: one launch over a pointer table of 2n (or n) vectors.
+static int builtin_plane_waves(ls_plan* P, int n, bool also_x, cudaStream_t st) {
+  Engine& e = P->eng;
+  std::vector<double> k;
+  builtin_kvec(P, n, k);
+  const int m = also_x ? 2 * n : n;
+  if (also_x) k.insert(k.end(), k.begin(), k.end());
+  std::vector<void*> ptrs(m);
+  for (int q = 0; q < n; ++q) {
+    ptrs[q] = e.vptr(V_B, q);
+    if (also_x) ptrs[n + q] = e.vptr(V_X, q);
+  }
+  // the kvec table holds 6 * cap doubles and the pointer tables 4 * cap pointers: tables 0 and 1 carry 2n
+  LS_CUDA_TRY(cudaMemcpyAsync(e.kvec_d, k.data(), k.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  int rc = engine_upload_ptrs(P, 0, (const void* const*)ptrs.data(), m, st);
+  if (rc) return rc;
+  PlaneWaveParams a{P->nx, P->ny, P->nz, P->h, e.kvec_d, (float2* const*)engine_ptr_table(P, 0)};
+  LS_CUDA_TRY(launch_plane_waves(a, m, st));
+  return LS_OK;
+}
+
 // Copy the caller's right-hand sides into slots [0, n) (b, and x0 = b unless initial guesses are given)
-// and set the slot states.
+// and set the slot states.  rhs == NULL: the plan's built-in plane waves.
 static int load_rhs(ls_plan* P, const float* f, int n, const ls_c64* const* rhs, int adjoint, cudaStream_t st,
                     const ls_c64* const* x0 = nullptr) {
   Engine& e = P->eng;
+  if (!rhs) {
+    int rc = builtin_plane_waves(P, n, x0 == nullptr, st);
+    if (rc) return rc;
+  }
   for (int q = 0; q < n; ++q) {
-    LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_B, q), rhs[q], e.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_X, q), x0 ? x0[q] : rhs[q], e.N * sizeof(float2),
-                                cudaMemcpyDeviceToDevice, st));
+    if (rhs) LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_B, q), rhs[q], e.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    if (rhs || x0)
+      LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_X, q), x0 ? x0[q] : rhs[q], e.N * sizeof(float2),
+                                  cudaMemcpyDeviceToDevice, st));
   }
   for (int q = 0; q < n; ++q) slot_defaults(P, e.slots_h[q], f, adjoint);
   return LS_OK;
@@ -1059,7 +1105,7 @@ static int forward_impl(ls_plan* P, const float* f, int n_views, const ls_c64* c
                         const ls_c64* const* x0, ls_c64* const* u_out, ls_c64* const* far, ls_stats* stats,
                         void* stream) {
   if (!P || !f || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
-  int rc = check_views(n_views, (const void* const*)u_in, "u_in", false);
+  int rc = check_views(n_views, (const void* const*)u_in, "u_in", true);
   if (!rc && x0) rc = check_views(n_views, (const void* const*)x0, "x0", false);
   if (!rc) rc = check_views(n_views, (const void* const*)u_out, "u_out", true);
   if (!rc) rc = check_views(n_views, (const void* const*)far, "far", true);
@@ -1228,7 +1274,7 @@ int ls_gradient(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_
                 void* stream) {
   if (!P || !f || !grad || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
   int rc = check_views(n_views, (const void* const*)residuals, "residuals", false);
-  if (!rc && !u_fwd) rc = check_views(n_views, (const void* const*)u_in, "u_in", false);
+  if (!rc && !u_fwd) rc = check_views(n_views, (const void* const*)u_in, "u_in", true);
   if (!rc && u_fwd) rc = check_views(n_views, (const void* const*)u_fwd, "u_fwd", false);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;

@@ -34,7 +34,7 @@ struct Engine {
   int* counts_d = nullptr;      // [0..3] slot counts (k_count), [4] device error flag (a wait gave up)
   int* counts_h = nullptr;      // pinned
   void** ptrs_d = nullptr;      // pointer tables: [4][cap]
-  double* kvec_d = nullptr;     // [cap*3]
+  double* kvec_d = nullptr;     // [cap*6]: wave vectors, 3 per view (twice for the built-in plane waves)
   float* weights_d = nullptr;   // [cap]
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t iter_graph = nullptr;

@@ -10,7 +10,7 @@
 //   x = x + alpha p + omega s;  r = s - omega t
 // The p/s updates run inside the first FFT pass and v/t inside the last one
 // (passes.cuh); this file holds the x/r update and the per-slot scalar logic.
-// Dot products: float32 products and per-thread partial sums, float64 from the warp shuffles up.
+// Dot products: float32 products and per-thread partial sums; every sum across threads in float64.
 #include "krylov.cuh"
 #include "passes.cuh"
 
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256, 4) k_update(UpdParams a) {
   float4* x = reinterpret_cast<float4*>(a.x + base);
   float4* r = reinterpret_cast<float4*>(a.r + base);
   const size_t n4 = a.n / 2;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float acc[3] = {0.f, 0.f, 0.f};
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
     float4 pv = __ldg(p + i), sv = __ldg(s + i), tv = __ldg(t + i), hv = __ldg(rh + i), xv = x[i];
     float2 p0 = make_float2(pv.x, pv.y), p1 = make_float2(pv.z, pv.w);
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256, 4) k_update(UpdParams a) {
     acc[1] += d0.y + d1.y;
     acc[2] += r0.x * r0.x + r0.y * r0.y + r1.x * r1.x + r1.y * r1.y;
   }
-  block_sum_store<4>(acc, a.partials + ((size_t)slot * gridDim.x + blockIdx.x) * 4);
+  block_sum_store<3>(acc, a.partials + ((size_t)slot * gridDim.x + blockIdx.x) * 4);
 }
 
 // ------------------------------------------------------------------ scalar steps
@@ -73,24 +73,24 @@ __global__ void __launch_bounds__(256) k_scalar(ScalarParams a) {
   SlotDev& sd = a.slots[slot];
   if (!(sd.flags & a.mask)) return;
   const double* part = a.partials + (size_t)slot * a.nparts * 4;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  // three partial sums per block (PH_RESID uses the first two)
+  double v[3] = {0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < a.nparts; i += blockDim.x) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] += part[(size_t)i * 4 + j];
+    for (int j = 0; j < 3; ++j) v[j] += part[(size_t)i * 4 + j];
   }
-  __shared__ double red[256][4];
+  __shared__ double red[256][3];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) red[threadIdx.x][j] = v[j];
+  for (int j = 0; j < 3; ++j) red[threadIdx.x][j] = v[j];
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) red[threadIdx.x][j] += red[threadIdx.x + o][j];
+      for (int j = 0; j < 3; ++j) red[threadIdx.x][j] += red[threadIdx.x + o][j];
     __syncthreads();
   }
   if (threadIdx.x != 0) return;
-  const double s0 = red[0][0], s1 = red[0][1], s2 = red[0][2], s3 = red[0][3];
-  (void)s3;
+  const double s0 = red[0][0], s1 = red[0][1], s2 = red[0][2];
   switch (a.phase) {
     case PH_RESID: {
       // partials: ||r||^2, ||b||^2 of r = b - A x
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) k_residual(ResidualParams a) {
   const float2* p = a.pred[q];
   const float2* m = a.meas[q];
   float2* r = a.res[q];
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float acc[2] = {0.f, 0.f};
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < a.count; i += (size_t)gridDim.x * blockDim.x) {
     const float2 d = csub(__ldg(p + i), __ldg(m + i));
     r[i] = d;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256) k_residual(ResidualParams a) {
     const float2 mm = __ldg(m + i);
     acc[1] += mm.x * mm.x + mm.y * mm.y;
   }
-  block_sum_store<4>(acc, a.partials + ((size_t)q * gridDim.x + blockIdx.x) * 4);
+  block_sum_store<2>(acc, a.partials + ((size_t)q * gridDim.x + blockIdx.x) * 4);
 }
 
 // <a, b> = sum conj(a) b per view (the inner product of the solver's scalars): float32 products and
@@ -321,13 +321,13 @@ __global__ void __launch_bounds__(256) k_inner(ResidualParams a) {
   const int q = blockIdx.y;
   const float2* x = a.pred[q];
   const float2* y = a.meas[q];
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float acc[2] = {0.f, 0.f};
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < a.count; i += (size_t)gridDim.x * blockDim.x) {
     const float2 d = cdotterm(__ldg(x + i), __ldg(y + i));
     acc[0] += d.x;
     acc[1] += d.y;
   }
-  block_sum_store<4>(acc, a.partials + ((size_t)q * gridDim.x + blockIdx.x) * 4);
+  block_sum_store<2>(acc, a.partials + ((size_t)q * gridDim.x + blockIdx.x) * 4);
 }
 
 // ------------------------------------------------------------------ launchers

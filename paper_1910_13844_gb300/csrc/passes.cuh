@@ -111,8 +111,14 @@ __device__ __forceinline__ void count_run(const SlotSel& s) {
 __device__ __forceinline__ void count_run_if(const SlotSel& s, bool first) {
   if (s.runs && first && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(s.runs, 1ull);
 }
-// Ordered list of the slots of this launch that run (every CTA builds the same list).
-// Block size must be a multiple of 32.  Returns the number of active slots.
+__device__ __forceinline__ int slot_adj(const SlotSel& s, int slot);
+
+// Ordered list of the slots of this launch that run (every CTA builds the same list).  An entry is
+// the slot index with the slot's adjoint flag in bit 16 (read once here, not in the view loops:
+// see active_slot / active_adj).  Block size must be a multiple of 32.  Returns the number of
+// active slots.
+__device__ __forceinline__ int active_slot(int e) { return e & 0xffff; }
+__device__ __forceinline__ bool active_adj(int e) { return (e >> 16) != 0; }
 __device__ __forceinline__ int build_active(const SlotSel& s, int* list, int* wsum) {
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nth = blockDim.x * blockDim.y;
@@ -142,7 +148,7 @@ __device__ __forceinline__ int build_active(const SlotSel& s, int* list, int* ws
   __syncthreads();
   int off = (w > 0 ? wsum[w - 1] : 0) + x - c;
   for (int i = beg; i < end; ++i)
-    if (slot_runs(s, i)) list[off++] = i;
+    if (slot_runs(s, i)) list[off++] = i | (slot_adj(s, i) ? 1 << 16 : 0);
   const int total = wsum[nw - 1];
   __syncthreads();
   return total;
@@ -185,38 +191,35 @@ struct Geo {
   static constexpr size_t smem_z = (size_t)(2 * L + L) * PS * sizeof(float2);   // exchange + Ghat + 2 staging halves
 };
 
-// Warp-then-block reduction of NV per-thread float partial sums; thread 0 writes doubles to
-// out[0..NV).  Each thread's partial is promoted to double before the first shuffle, so every sum
-// across threads (warp shuffles and the block level) is accumulated in float64.
+// Block reduction of NV per-thread float partial sums; thread 0 writes doubles to out[0..NV).
+// Every sum across threads is float64: the partials are gathered in shared memory, each lane of
+// the first warp adds a strided share of them in float64, and a float64 warp-shuffle tree combines
+// the 32 lanes.  Only one warp issues float64 instructions (GB300's float64 rate is low: a shuffle
+// tree in every warp cost the last FFT pass a quarter of its speed).  Blocks of at most 256
+// threads; one call per kernel (the shared array is not guarded against reuse).
 template <int NV>
 __device__ __forceinline__ void block_sum_store(const float (&acc)[NV], double* out) {
-  double d[NV];
-#pragma unroll
-  for (int j = 0; j < NV; ++j) d[j] = (double)acc[j];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int j = 0; j < NV; ++j) d[j] += __shfl_xor_sync(0xffffffffu, d[j], o);
-  __shared__ double wsum[32][NV];
+  constexpr int kMaxThreads = 256;
+  __shared__ float part[NV][kMaxThreads];
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
-  const int lane = tid & 31, w = tid >> 5, nw = (nthreads + 31) >> 5;
-  __syncthreads();
-  if (lane == 0)
 #pragma unroll
-    for (int j = 0; j < NV; ++j) wsum[w][j] = d[j];
+  for (int j = 0; j < NV; ++j) part[j][tid] = acc[j];
   __syncthreads();
-  if (w == 0) {
-    double v[NV];
+  if (tid < 32) {
+    double d[NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = lane < nw ? wsum[lane][j] : 0.0;
+    for (int j = 0; j < NV; ++j) d[j] = 0.0;
+    for (int i = tid; i < nthreads; i += 32)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) d[j] += (double)part[j][i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-      for (int j = 0; j < NV; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
-    if (lane == 0)
+      for (int j = 0; j < NV; ++j) d[j] += __shfl_xor_sync(0xffffffffu, d[j], o);
+    if (tid == 0)
 #pragma unroll
-      for (int j = 0; j < NV; ++j) out[j] = v[j];
+      for (int j = 0; j < NV; ++j) out[j] = d[j];
   }
 }
 
@@ -412,12 +415,13 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS, Geo<L>::ZMINB) k_z(ZPa
       if (kx0 + j < ncont) cp_async16(&buf[z * P + j], base + (size_t)z * zstride + j);
     }
   };
-  stage_view(s_list[0], stage);
+  stage_view(active_slot(s_list[0]), stage);
   cp_async_commit();
 #pragma unroll 1
   for (int iv = 0; iv < nact; ++iv) {
-    const int slot = s_list[iv];
-    if (iv + 1 < nact) stage_view(s_list[iv + 1], stage + ((iv + 1) & 1) * NZ * P);
+    const int slot = active_slot(s_list[iv]);
+    const bool adj = active_adj(s_list[iv]);
+    if (iv + 1 < nact) stage_view(active_slot(s_list[iv + 1]), stage + ((iv + 1) & 1) * NZ * P);
     cp_async_commit();
     cp_async_wait<1>();   // every group but the newest: this view's pencils (and the Ghat tile)
     __syncthreads();
@@ -450,7 +454,6 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS, Geo<L>::ZMINB) k_z(ZPa
       for (int n2 = 0; n2 < R2; ++n2) u[n2] = xs[(t * R2 + n2) * P + p];
       Dft<R2, -1>::run(u);
       // Green multiply: u[k2] holds kz = t + R1 k2
-      const bool adj = slot_adj(a.sel, slot) != 0;
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) {
         const float2 gv = gs[(t + R1 * k2) * P + p];
@@ -653,7 +656,7 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
     mbar_init_fence();
     for (int k = 0; k < NS && k < nact; ++k) {
       mbar_expect_tx(&full[k], (unsigned)W::stage_bytes);
-      tma_load_4d(stage + (size_t)k * NZ * P, &a.tmap, &full[k], 2 * kx0, ky, 0, a.slot0 + s_list[k]);
+      tma_load_4d(stage + (size_t)k * NZ * P, &a.tmap, &full[k], 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[k]));
     }
   }
   // Ghat tile with kz folded into [0, NZ] (Ghat is even in every axis), and the stage twiddles
@@ -677,12 +680,12 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
       const int buf = iv % NS;
       if (!mbar_wait_abort(&done[buf], (unsigned)(iv / NS) & 1u, &s_abort, limit_ns)) break;
       float2* sb = stage + (size_t)buf * NZ * P;
-      tma_store_4d(&a.tmap, sb, 2 * kx0, ky, 0, a.slot0 + s_list[iv]);
+      tma_store_4d(&a.tmap, sb, 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[iv]));
       bulk_commit();
       if (iv + NS < nact) {
         bulk_wait_read_all();   // the store has read the buffer
         mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
-        tma_load_4d(sb, &a.tmap, &full[buf], 2 * kx0, ky, 0, a.slot0 + s_list[iv + NS]);
+        tma_load_4d(sb, &a.tmap, &full[buf], 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[iv + NS]));
       }
     }
     bulk_wait_read_all();
@@ -716,7 +719,6 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
 #pragma unroll 1
   for (int iv = 0; iv < nact; ++iv) {
     const int buf = iv % NS;
-    const int slot = s_list[iv];
     const bool ok = (a.stall && iv == 0) ? mbar_wait_abort(never, 0u, &s_abort, limit_ns)
                                          : mbar_wait_abort(&full[buf], (unsigned)(iv / NS) & 1u, &s_abort, limit_ns);
     if (!__all_sync(0xffffffffu, ok)) break;
@@ -751,15 +753,17 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
         u[2 * i + 1] = make_float2(q.z, q.w);
       }
       Dft<R2, -1>::run(u);
+      // the adjoint flag is read from the active list where it is used (not held across the stages)
+      const bool adj = active_adj(s_list[iv]);
       if constexpr (GREG) {
-        if (slot_adj(a.sel, slot)) {
+        if (adj) {
 #pragma unroll
           for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmulc(u[k2], g[k2]);
         } else {
 #pragma unroll
           for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmul(u[k2], g[k2]);
         }
-      } else if (slot_adj(a.sel, slot)) {
+      } else if (adj) {
         green_mul<true, R1, R2, L, W::GR>(u, gc, t);
       } else {
         green_mul<false, R1, R2, L, W::GR>(u, gc, t);
@@ -842,7 +846,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
     for (int k1 = 0; k1 < R1; ++k1) S[k1 * G::SROW + t] = v[k1];
   }
   __syncthreads();
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float acc[3] = {0.f, 0.f, 0.f};
   if (valid && t < R1) {
     float2 u[R2];
 #pragma unroll
@@ -889,7 +893,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
     }
   }
   if (a.mode >= IX_BICG_V) {
-    block_sum_store<4>(acc, a.partials + ((size_t)slot * gridDim.x + blockIdx.x) * 4);
+    block_sum_store<3>(acc, a.partials + ((size_t)slot * gridDim.x + blockIdx.x) * 4);
   }
 }
 

@@ -30,9 +30,13 @@ def allreduce_(t: torch.Tensor, group=None) -> torch.Tensor:
     return t
 
 
-def data_grad_sharded(prob, f: torch.Tensor, group=None):
-    """(loss, gradient) of the data term over all views, each rank solving its own shard."""
-    from .recon import data_grad
+def data_grad_sharded(prob, f: torch.Tensor, group=None, data_grad=None):
+    """(loss, gradient) of the data term over all views, each rank solving its own shard.
+
+    ``data_grad(prob, f, views) -> (loss, grad)`` evaluates the term over a list of views; the
+    default is the CUDA library's (``recon.data_grad``)."""
+    if data_grad is None:
+        from .recon import data_grad
 
     world = dist.get_world_size(group) if dist.is_initialized() else 1
     rank = dist.get_rank(group) if dist.is_initialized() else 0

@@ -111,3 +111,33 @@ def test_not_converged_status_is_reported():
     assert code == ls.LS_NOT_CONVERGED
     assert stats[0]["iterations"] == 2
     plan.close()
+
+
+@pytest.mark.gpu
+def test_builtin_plane_waves_equal_explicit_incident_fields():
+    # u_in == NULL: the plan's cone of plane waves (sin theta = NA / eta_b, phi_q = 2 pi q / Q), generated in
+    # the solver's workspace; the same solve with the explicit fields, and the oracle's
+    torch, ls = torch_and_lib()
+    shape = (24, 32, 32)
+    Q = 3
+    f64 = potential(ph.random_ellipsoids(shape, count=3, rmin=2, rmax=6, seed=31))
+    f = to_dev(torch, f64, torch.float32)
+    plan = ls.Plan(shape, KB, H, tol=1e-6, cone_sin_theta=0.8 / ETA_B)
+    kvec = ph.cone_directions(Q, 0.8) * KB
+    u_ref, far_ref, code_ref, _ = plan.forward(f, plan.plane_waves(kvec))
+    u, far, code, stats = plan.forward(f, None, n_views=Q)
+    torch.cuda.synchronize()
+    assert code == ls.LS_OK and code_ref == ls.LS_OK
+    assert rel(u.cpu().numpy(), u_ref.cpu().numpy()) < 1e-6
+    assert rel(far.cpu().numpy(), far_ref.cpu().numpy()) < 1e-6
+    for q, (uin_o, u_o, far_o) in enumerate(_oracle_views(shape, f64, kvec)):
+        assert rel(u[q].cpu().numpy(), u_o) < TOL_FIELD
+        assert rel(far[q].cpu().numpy(), far_o) < TOL_FIELD
+    # the gradient recomputes its forward fields from the built-in waves when u_in and u_fwd are NULL
+    res = far.clone()
+    g_ref, _, _ = plan.gradient(f, res, u_fwd=u_ref)
+    g, code, _ = plan.gradient(f, res)
+    torch.cuda.synchronize()
+    assert code == ls.LS_OK
+    assert rel(g.cpu().numpy(), g_ref.cpu().numpy()) < 1e-5
+    plan.close()

@@ -108,7 +108,7 @@ def test_gradient_matches_central_differences():
     _, g = loss_and_grad(f0, True)
     rng = np.random.default_rng(3)
     d = rng.uniform(-1, 1, shape) * (f_true > 0)
-    eps = 1e-3 * np.max(np.abs(f_true)) * 10
+    eps = 1e-3 * np.max(np.abs(f_true))   # the step of the central difference (1e-3 of max |f|)
     Lp, _ = loss_and_grad(f0 + eps * d, False)
     Lm, _ = loss_and_grad(f0 - eps * d, False)
     fd = (Lp - Lm) / (2 * eps)
