@@ -121,8 +121,8 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
-Z_SOURCES = ["paper_1910_13844_gb300/csrc/passes.cuh", "paper_1910_13844_gb300/csrc/dft.cuh",
-             "paper_1910_13844_gb300/csrc/common.cuh"]
+Z_SOURCES = ["paper_1910_13844_gb300/csrc/zpass.cuh", "paper_1910_13844_gb300/csrc/pass_common.cuh",
+             "paper_1910_13844_gb300/csrc/dft.cuh", "paper_1910_13844_gb300/csrc/common.cuh"]
 
 
 def opcodes_per_slot(kernel: str):

@@ -1,15 +1,17 @@
 // Measured FP32 throughput of the current device (ls_fp32_peak): the denominator of the FP32-pipe
 // roofline of the FFT passes.  Three kernels of known operation counts -- scalar FFMA, scalar FMUL
 // and packed add.f32x2 -- each run eight independent dependency chains per thread over a grid of
-// eight 256-thread blocks per SM, timed with CUDA events after one untimed launch.
+// eight 256-thread blocks per SM, eight dependent steps per chain and loop iteration, timed with
+// CUDA events after one untimed launch.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
 
 namespace lsgpu {
 
-constexpr int kPeakIters = 4096;
+constexpr int kPeakIters = 1024;
 constexpr int kPeakChains = 8;
+constexpr int kPeakReps = 8;   // dependent steps of each chain per loop iteration (loop overhead < 3%)
 
 template <int OP>
 __global__ void __launch_bounds__(256) k_peak(float seed, float* sink) {
@@ -28,9 +30,9 @@ __global__ void __launch_bounds__(256) k_peak(float seed, float* sink) {
 #pragma unroll 1
     for (int it = 0; it < kPeakIters; ++it) {
 #pragma unroll
-      for (int j = 0; j < kPeakChains / 2; ++j) asm volatile("add.rn.f32x2 %0, %0, %1;" : "+l"(p[j]) : "l"(q));
+      for (int r = 0; r < kPeakReps; ++r)
 #pragma unroll
-      for (int j = 0; j < kPeakChains / 2; ++j) asm volatile("add.rn.f32x2 %0, %0, %1;" : "+l"(p[j]) : "l"(q));
+        for (int j = 0; j < kPeakChains / 2; ++j) asm volatile("add.rn.f32x2 %0, %0, %1;" : "+l"(p[j]) : "l"(q));
     }
 #pragma unroll
     for (int j = 0; j < kPeakChains / 2; ++j) asm("mov.b64 {%0, %1}, %2;" : "=f"(a[2 * j]), "=f"(a[2 * j + 1]) : "l"(p[j]));
@@ -38,7 +40,7 @@ __global__ void __launch_bounds__(256) k_peak(float seed, float* sink) {
 #pragma unroll 1
     for (int it = 0; it < kPeakIters; ++it) {
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
+      for (int r = 0; r < kPeakReps; ++r)
 #pragma unroll
         for (int j = 0; j < kPeakChains; ++j) {
           if constexpr (OP == 0) asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(a[j]) : "f"(b), "f"(c));
@@ -68,8 +70,9 @@ extern "C" int ls_fp32_peak(double* out, void* stream) {
   LS_CUDA_TRY(cudaEventCreate(&e0));
   LS_CUDA_TRY(cudaEventCreate(&e1));
   const int blocks = 8 * sms, threads = 256;
-  // lane operations per launch: 2 * chains per iteration (FFMA, FMUL: one lane-op each; packed add: two)
-  const double lane_ops = (double)blocks * threads * kPeakIters * 2.0 * kPeakChains;
+  // lane operations per thread and iteration: reps * chains (FFMA, FMUL: reps * chains instructions of one
+  // lane-op; packed add: reps * chains / 2 instructions of two)
+  const double lane_ops = (double)blocks * threads * kPeakIters * kPeakReps * kPeakChains;
   int rc = LS_OK;
   for (int op = 0; op < 3 && rc == LS_OK; ++op) {
     auto launch = [&] {
