@@ -327,6 +327,11 @@ struct PassImpl {
         k_zw<L><<<(2 * a.nx / ZW<L>::P) * (2 * a.ny), ZW<L>::NT, ZW<L>::smem, st>>>(a);
         return;
       }
+    } else if constexpr (ZG<L>::ok) {
+      if (a.use_tma && (2 * a.nx) % ZG<L>::P == 0 && a.nz <= 256) {
+        k_zg<L><<<(2 * a.nx / ZG<L>::P) * (2 * a.ny), ZG<L>::NT, ZG<L>::smem, st>>>(a);
+        return;
+      }
     }
     dim3 blk(G::PS, G::T), grd(((2 * a.nx + G::PS - 1) / G::PS) * (2 * a.ny));
     k_z<L><<<grd, blk, G::smem_z, st>>>(a);
@@ -341,6 +346,8 @@ struct PassImpl {
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_z);
       if constexpr (ZW<L>::ok)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zw<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZW<L>::smem);
+      if constexpr (ZG<L>::ok)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zg<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZG<L>::smem);
     }
     return e;
   }

@@ -476,4 +476,262 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
 #undef LS_ZW_LIMIT
 }
 
+// ------------------------------------------------------------------------- Z (TMA-staged, column groups)
+// The TMA-staged z pass for lengths whose balanced split has a thread count that does not divide 32
+// (the bead lengths 144 = 12 x 12 and 288 = 12 x 24).  T = R1 = 12 threads per column; a group of
+// WG = 3 warps (96 threads) owns CG = 8 whole columns, so no lane idles; two groups per CTA cover the
+// 16 columns of one TMA box.  A column's threads span the warps of its group, so its exchanges are
+// ordered by a named barrier of the group, and the group agrees on every wait's outcome with a
+// barrier reduction (no thread of a group can leave the view loop while another waits at a group
+// barrier).  Stage 1 and the last inverse stage give each thread S1 = R2 / T sub-transforms of
+// length R1; stage 2 and the first inverse stage one of length R2.  Producer warp, view buffers,
+// Green values in registers and the waits' limits are those of k_zw.
+template <int L> struct ZGRadix { static constexpr bool ok = false; static constexpr int R1 = 2, R2 = 2, NS = 1, MINB = 1; };
+template <> struct ZGRadix<144> { static constexpr bool ok = true; static constexpr int R1 = 12, R2 = 12, NS = 4, MINB = 3; };
+template <> struct ZGRadix<288> { static constexpr bool ok = true; static constexpr int R1 = 12, R2 = 24, NS = 3, MINB = 2; };
+
+template <int L>
+struct ZG {
+  static constexpr bool ok = ZGRadix<L>::ok;
+  static constexpr int R1 = ZGRadix<L>::R1, R2 = ZGRadix<L>::R2;
+  static constexpr int T = R1;                   // threads per column
+  static constexpr int S1 = R2 / T;              // stage-1 sub-transforms per thread
+  static constexpr int CG = 8, WG = 3;           // columns and warps of a group: CG * T == 32 * WG
+  static constexpr int P = 16;                   // columns per CTA: one 128-byte TMA row
+  static constexpr int NGRP = P / CG;
+  static constexpr int NW = NGRP * WG;           // compute warps
+  static constexpr int NT = 32 * NW + 32;        // + one producer warp
+  static constexpr int NZ = L / 2;
+  static constexpr int NS = ZGRadix<L>::NS, MINB = ZGRadix<L>::MINB;
+  // exchange rows of R + 2 entries, read with 16-byte loads; per-column pitch congruent to 2 mod 16
+  // (float2 units): the 8 columns of a quarter-warp's 16-byte reads, and the two rows by eight
+  // columns of a half-warp's 8-byte writes, fall on disjoint banks
+  static constexpr int RA = R2 + 2, RB = R1 + 2;
+  static constexpr int pitch(int n) { return n + ((2 - n % 16) % 16 + 16) % 16; }
+  static constexpr int XP = pitch(imax(R1 * RA, R2 * RB));
+  // Green rows [kz][P + 8]: the two rows of a half-warp's reads are 8 words apart
+  static constexpr int GR = P + 8;
+  static constexpr int TWA = R1 + 2, TWB = R2 + 2;
+  static constexpr size_t r16(size_t b) { return (b + 15) / 16 * 16; }
+  static constexpr size_t stage_bytes = (size_t)NZ * P * sizeof(float2);
+  static constexpr size_t g_bytes = r16((size_t)(NZ + 1) * GR * sizeof(float2));
+  static constexpr size_t x_bytes = r16((size_t)P * XP * sizeof(float2));
+  static constexpr size_t off_g = NS * stage_bytes;   // the Green tile and the exchange area overlay
+  static constexpr size_t off_x = off_g;
+  static constexpr size_t off_twa = off_g + (g_bytes > x_bytes ? g_bytes : x_bytes);
+  static constexpr size_t off_twb = off_twa + r16((size_t)R2 * TWA * sizeof(float2));
+  static constexpr size_t off_bar = off_twb + r16((size_t)R1 * TWB * sizeof(float2));
+  static constexpr int NBAR = 2 * NS + 1;                                     // full[NS], done[NS], never
+  static constexpr size_t smem = off_bar + NBAR * sizeof(uint64_t) + 1024;    // + room to align the base to 1024
+};
+
+// Barrier of N threads on named barrier ID (N a multiple of 32, warp-uniform calls).
+template <int ID, int N>
+__device__ __forceinline__ void named_sync() {
+  asm volatile("bar.sync %0, %1;\n" ::"n"(ID), "n"(N) : "memory");
+}
+// The same barrier, returning the AND of `v` over the participating threads.
+template <int ID, int N>
+__device__ __forceinline__ bool named_all(bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.and.pred po, %2, %3, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+      : "=r"(r) : "r"((unsigned)v), "n"(ID), "n"(N) : "memory");
+  return r != 0;
+}
+// Group barriers of the column-group z pass: named barriers 2 + group (0 is __syncthreads, 1 the
+// compute warps' barrier).
+template <int NGRP, int N>
+__device__ __forceinline__ void group_sync(int gi) {
+  static_assert(NGRP == 2, "two column groups per CTA");
+  if (gi == 0) named_sync<2, N>();
+  else named_sync<3, N>();
+}
+template <int NGRP, int N>
+__device__ __forceinline__ bool group_all(int gi, bool v) {
+  static_assert(NGRP == 2, "two column groups per CTA");
+  return gi == 0 ? named_all<2, N>(v) : named_all<3, N>(v);
+}
+
+template <int L>
+__global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_constant__ ZParams a) {
+  using W = ZG<L>;
+  constexpr int R1 = W::R1, R2 = W::R2, P = W::P, NZ = W::NZ, T = W::T, S1 = W::S1, CG = W::CG, WG = W::WG,
+                NW = W::NW, NS = W::NS, RA = W::RA, RB = W::RB;
+  static_assert(W::ok && CG * T == 32 * WG && R2 % T == 0, "k_zg split");
+  static_assert(R1 % 2 == 0 && R2 % 2 == 0 && W::XP % 2 == 0, "16-byte exchange reads need even rows");
+  extern __shared__ __align__(16) unsigned char zg_raw[];
+  const unsigned raw = smem_addr(zg_raw);
+  unsigned char* base = zg_raw + (((raw + 1023u) & ~1023u) - raw);
+  float2* stage = reinterpret_cast<float2*>(base);
+  float2* gs = reinterpret_cast<float2*>(base + W::off_g);
+  float2* xs = reinterpret_cast<float2*>(base + W::off_x);
+  float2* twa = reinterpret_cast<float2*>(base + W::off_twa);
+  float2* twb = reinterpret_cast<float2*>(base + W::off_twb);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);   // [NS]: a view's tile has landed
+  uint64_t* done = full + NS;                                         // [NS]: the compute warps are done with it
+  uint64_t* never = done + NS;                                        // no thread arrives on it (stall test)
+  __shared__ int s_list[kMaxLaunchSlots];
+  __shared__ int s_ws[32];
+  __shared__ int s_abort;
+  const int nact = build_active(a.sel, s_list, s_ws);
+  if (nact == 0) return;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int ncont = 2 * a.nx;
+  const int tiles_c = ncont / P;
+  const int ky = blockIdx.x / tiles_c;
+  const int kx0 = (blockIdx.x % tiles_c) * P;
+  const bool producer = warp == NW;
+#define LS_ZG_LIMIT (a.wait_ns ? a.wait_ns : 1000000000ull)
+  if (producer && lane == 0) {
+    s_abort = 0;
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&done[k], NW);
+    }
+    mbar_init(never, 1);
+    mbar_init_fence();
+    for (int k = 0; k < NS && k < nact; ++k) {
+      mbar_expect_tx(&full[k], (unsigned)W::stage_bytes);
+      tma_load_4d(stage + (size_t)k * NZ * P, &a.tmap, &full[k], 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[k]));
+    }
+  }
+  // Ghat tile with kz folded into [0, NZ] (Ghat is even in every axis), and the stage twiddles
+  const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
+  for (int i = tid; i < (NZ + 1) * P; i += W::NT) {
+    const int kz = i / P, cc = i % P, kx = kx0 + cc;
+    const int fx = kx <= a.nx ? kx : ncont - kx;
+    gs[kz * W::GR + cc] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+  }
+  for (int i = tid; i < R1 * R2; i += W::NT) {
+    twa[(i / R1) * W::TWA + i % R1] = __ldg(a.zwa + i);
+    twb[(i / R2) * W::TWB + i % R2] = __ldg(a.zwb + i);
+  }
+  __syncthreads();
+  if (producer) {
+    // producer: after the compute warps release a view's buffer, store it and refill it with the
+    // view NS ahead
+    if (lane != 0) return;
+    int iv = 0;
+    for (; iv < nact; ++iv) {
+      const int buf = iv % NS;
+      if (!mbar_wait_abort(&done[buf], (unsigned)(iv / NS) & 1u, &s_abort, LS_ZG_LIMIT, 2000u)) break;
+      float2* sb = stage + (size_t)buf * NZ * P;
+      tma_store_4d(&a.tmap, sb, 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[iv]));
+      bulk_commit();
+      if (iv + NS < nact) {
+        bulk_wait_read_all();   // the store has read the buffer
+        mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
+        tma_load_4d(sb, &a.tmap, &full[buf], 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[iv + NS]));
+      }
+    }
+    bulk_wait_read_all();
+    if (iv < nact) {
+      // gave up at view iv: flag it, and give the loads still in flight into this CTA's buffers
+      // (views iv .. iv + NS - 1, all issued) a bounded time to land (one second each, whatever
+      // the per-view limit)
+      atomicExch(a.err, 1);
+      for (int j = iv; j < iv + NS && j < nact; ++j) mbar_wait(&full[j % NS], (unsigned)(j / NS) & 1u);
+    }
+    return;
+  }
+  // compute warps: group gi of WG warps owns columns [gi CG, gi CG + CG); thread (t, c) of the group
+  const int gi = warp / WG;
+  const int g = (warp % WG) * 32 + lane;
+  const int t = g / CG, c = g % CG;
+  const int cc = gi * CG + c;
+  float2* xc = xs + cc * W::XP;
+  const float2* gc = gs + cc;
+  // this thread's Green values (kz = t + R1 k2, the same for every view) in registers
+  float2 gr[R2];
+#pragma unroll
+  for (int k2 = 0; k2 < R2; ++k2) gr[k2] = k2 < R2 / 2 ? gc[(t + R1 * k2) * W::GR] : gc[(L - R1 * k2 - t) * W::GR];
+  // the exchange area overlays the Green tile: every compute warp has its values before any writes
+  named_sync<1, NW * 32>();
+  bool next_ready = false;
+#pragma unroll 1
+  for (int iv = 0; iv < nact; ++iv) {
+    const int buf = iv % NS;
+    const bool ok = (a.stall && iv == 0) ? mbar_wait_abort(never, 0u, &s_abort, LS_ZG_LIMIT)
+                    : next_ready         ? true
+                                         : mbar_wait_abort(&full[buf], (unsigned)(iv / NS) & 1u, &s_abort, LS_ZG_LIMIT);
+    // the group agrees (this is also the barrier that frees the exchange area of the previous view)
+    if (!group_all<W::NGRP, WG * 32>(gi, ok)) break;
+    next_ready = iv + 1 < nact && mbar_test_wait(&full[(iv + 1) % NS], (unsigned)((iv + 1) / NS) & 1u);
+    count_run(a.sel);
+    unsigned char* sb = reinterpret_cast<unsigned char*>(stage + (size_t)buf * NZ * P);
+    // forward stage 1: sub-transforms n2 = t + T s, inputs z = R2 n1 + n2 (n1 < R1/2: z < nz)
+#pragma unroll
+    for (int s = 0; s < S1; ++s) {
+      const int n2 = t + T * s;
+      float2 v[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int n1 = 0; n1 < R1 / 2; ++n1) v[n1] = *reinterpret_cast<const float2*>(sb + swz128(R2 * n1 + n2, cc));
+      Dft<R1, -1, R1 / 2, R1>::run(v);
+      const float4* tw4 = reinterpret_cast<const float4*>(twa + n2 * W::TWA);
+#pragma unroll
+      for (int k = 0; k < R1 / 2; ++k) {
+        const float4 w = tw4[k];
+        if (k > 0) v[2 * k] = cmul(v[2 * k], make_float2(w.x, w.y));
+        v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
+      }
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) xc[k1 * RA + n2] = v[k1];
+    }
+    group_sync<W::NGRP, WG * 32>(gi);
+    // forward stage 2 (thread t = k1), Green multiply, inverse stage 1 (transposed split)
+    float2 u[R2];
+#pragma unroll
+    for (int i = 0; i < R2 / 2; ++i) {
+      const float4 q = *reinterpret_cast<const float4*>(xc + t * RA + 2 * i);
+      u[2 * i] = make_float2(q.x, q.y);
+      u[2 * i + 1] = make_float2(q.z, q.w);
+    }
+    Dft<R2, -1>::run(u);
+    if (active_adj(s_list[iv])) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmulc(u[k2], gr[k2]);
+    } else {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmul(u[k2], gr[k2]);
+    }
+    Dft<R2, +1>::run(u);
+    {
+      const float4* tw4 = reinterpret_cast<const float4*>(twb + t * W::TWB);
+#pragma unroll
+      for (int k = 0; k < R2 / 2; ++k) {
+        const float4 w = tw4[k];
+        if (k > 0) u[2 * k] = cmulc(u[2 * k], make_float2(w.x, w.y));
+        u[2 * k + 1] = cmulc(u[2 * k + 1], make_float2(w.z, w.w));
+      }
+    }
+    group_sync<W::NGRP, WG * 32>(gi);   // every thread of the group has read its stage-1 row
+#pragma unroll
+    for (int j1 = 0; j1 < R2; ++j1) xc[j1 * RB + t] = u[j1];
+    group_sync<W::NGRP, WG * 32>(gi);
+    // inverse stage 2: sub-transforms j1 = t + T s; outputs z = j1 + R2 j2 (j2 < R1/2: z < nz), in place
+#pragma unroll
+    for (int s = 0; s < S1; ++s) {
+      const int j1 = t + T * s;
+      float2 w[R1];
+#pragma unroll
+      for (int i = 0; i < R1 / 2; ++i) {
+        const float4 q = *reinterpret_cast<const float4*>(xc + j1 * RB + 2 * i);
+        w[2 * i] = make_float2(q.x, q.y);
+        w[2 * i + 1] = make_float2(q.z, q.w);
+      }
+      Dft<R1, +1, R1, R1 / 2>::run(w);
+#pragma unroll
+      for (int j2 = 0; j2 < R1 / 2; ++j2) *reinterpret_cast<float2*>(sb + swz128(j1 + R2 * j2, cc)) = w[j2];
+    }
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&done[buf]);
+  }
+#undef LS_ZG_LIMIT
+}
+
 }  // namespace lsgpu

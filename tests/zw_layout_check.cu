@@ -45,7 +45,35 @@ void check() {
   printf("L=%3d split %2dx%-2d NS=%d smem %6zu B x %d CTAs/SM\n", L, W::R1, W::R2, W::NS, W::smem, W::MINB);
 }
 
+// The column-group z pass (k_zg): the same layout rules, plus the thread mapping of its groups.
+template <int L>
+void check_groups() {
+  using W = ZG<L>;
+  if (!W::ok) return;
+  constexpr size_t static_smem = kMaxLaunchSlots * sizeof(int) + 32 * sizeof(int) + 16;
+  constexpr size_t sm_capacity = 228 * 1024, per_cta_max = 227 * 1024, reserved_per_cta = 1024;
+  REQUIRE(W::CG * W::T == 32 * W::WG && W::NGRP * W::CG == W::P && W::R2 % W::T == 0 && W::R1 == W::T, L);
+  REQUIRE(W::stage_bytes % 1024 == 0, L);
+  REQUIRE(W::off_g % 16 == 0 && W::off_twa % 16 == 0 && W::off_twb % 16 == 0 && W::off_bar % 16 == 0, L);
+  REQUIRE(W::off_g >= (size_t)W::NS * W::stage_bytes, L);
+  REQUIRE(W::off_twa >= W::off_g + W::g_bytes && W::off_twa >= W::off_x + W::x_bytes, L);
+  REQUIRE(W::off_twb >= W::off_twa + (size_t)W::R2 * W::TWA * sizeof(float2), L);
+  REQUIRE(W::off_bar >= W::off_twb + (size_t)W::R1 * W::TWB * sizeof(float2), L);
+  REQUIRE(W::NBAR == 2 * W::NS + 1 && W::smem >= W::off_bar + W::NBAR * sizeof(uint64_t) + 1023, L);
+  REQUIRE(W::R1 * W::RA <= W::XP && W::R2 * W::RB <= W::XP, L);
+  REQUIRE(W::XP % 16 == 2 && W::RA % 2 == 0 && W::RB % 2 == 0, L);
+  REQUIRE((size_t)W::P * W::XP * sizeof(float2) <= W::x_bytes, L);
+  REQUIRE(W::GR % 16 == 8 && W::GR >= W::P, L);
+  REQUIRE(W::smem <= per_cta_max, L);
+  REQUIRE((size_t)W::MINB * (W::smem + static_smem + reserved_per_cta) <= sm_capacity, L);
+  // every row read from the stage buffer and every output row lies in the tile
+  REQUIRE(W::R2 * (W::R1 / 2 - 1) + (W::R2 - 1) < W::NZ, L);
+  printf("L=%3d groups %dx%d (T=%d, S1=%d) NS=%d smem %6zu B x %d CTAs/SM\n", L, W::R1, W::R2, W::T, W::S1, W::NS,
+         W::smem, W::MINB);
+}
+
 int main() {
+  check_groups<144>(); check_groups<288>();
   check<16>(); check<24>(); check<32>(); check<48>(); check<64>(); check<96>(); check<128>();
   check<144>(); check<192>(); check<256>(); check<288>(); check<384>();
   printf(failures ? "FAIL\n" : "OK\n");
