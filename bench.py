@@ -792,7 +792,8 @@ def run_bead_mode(args):
                 "mean_iterations": float(np.mean(its)),
                 "worst_status": int(max(c for c, _ in stats)),
                 "z_pass_gbs": round(z_gbs, 1) if z_gbs else None,
-                "z_kernel": "k_z (cp.async staging)" if 2 * n in (144, 288) else "k_zw",
+                "z_kernel": ("k_zg (TMA-staged column groups)" if tune["z_tma"] else "k_z (cp.async staging)")
+                if 2 * n in (144, 288) else ("k_zw" if tune["z_tma"] else "k_z (cp.async staging)"),
                 "autotune": {k: tune[k] for k in ("z_tma", "ix_prefetch", "fx_views_fastest", "check_every",
                                                   "use_graphs")},
             }

@@ -313,6 +313,7 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   z.zwa = P->zwa_z;
   z.zwb = P->zwb_z;
   z.wait_ns = (unsigned long long)P->inj_z_wait_ns;
+  z.sms = P->sms;
   z.stall = P->inj_z_stall;
   timed(P, LS_K_Z, nslots, st, [&] { P->pz.z(z, nslots, st); });
   StridedParams iy = fy_base(P, counted(P, sel, LS_K_IY), e.a2, e.a2_stride, e.a1, e.a1_stride, P->nz);
@@ -532,6 +533,7 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   v.tw2_x = P->tw2_x; v.tw_y = P->tw_y;
   v.twa_z = P->twa_z; v.twb_z = P->twb_z; v.zwa_z = P->zwa_z; v.zwb_z = P->zwb_z;
   v.gocta = P->gocta; v.k2hat = P->k2hat; v.p_built = P->p_built;
+  v.device = P->device; v.sms = P->sms;
   v.tune_z_tma = P->tune_z_tma; v.tune_ix_prefetch = P->tune_ix_prefetch;
   v.tune_fx_views_fastest = P->tune_fx_views_fastest;
   const Engine& e = P->eng;
@@ -562,6 +564,7 @@ ls_plan* plan_clone_shared(const ls_plan* P) {
   c->tw2_x = P->tw2_x; c->tw_y = P->tw_y;
   c->twa_z = P->twa_z; c->twb_z = P->twb_z; c->zwa_z = P->zwa_z; c->zwb_z = P->zwb_z;
   c->gocta = P->gocta; c->k2hat = P->k2hat; c->p_built = P->p_built;
+  c->device = P->device; c->sms = P->sms;
   c->tune_z_tma = P->tune_z_tma; c->tune_ix_prefetch = P->tune_ix_prefetch;
   c->tune_fx_views_fastest = P->tune_fx_views_fastest;
   c->owns_shared = false;
@@ -840,7 +843,8 @@ int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel, c
   P->x_gamma = P->opt.x_gamma > 0 ? P->opt.x_gamma : 0.75 * P->nz * P->h;
   int rc = LS_OK;
   cudaError_t se = cudaSuccess;
-  if (cudaGetDevice(&P->device) != cudaSuccess) {
+  if (cudaGetDevice(&P->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess) {
     set_last_error("no current CUDA device");
     delete P;
     return LS_ECUDA;

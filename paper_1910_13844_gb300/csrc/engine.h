@@ -84,6 +84,7 @@ struct ls_plan {
   // ls_matvec_noalloc: device address of the library's static scratch array on this plan's device,
   // looked up when the plan is created (null, with noalloc_rc set, if that failed)
   int device = 0;
+  int sms = 0;                   // SMs of the plan's device (grid size of the persistent z passes)
   void* noalloc_scratch = nullptr;
   int noalloc_rc = 0;
   lsgpu::Engine eng;

@@ -64,6 +64,7 @@ struct ZParams {
   int slot0;                   // slot coordinate of this launch's slot 0 in tmap
   int* err;                    // set to 1 if a wait for a TMA copy gave up (the launch's output is invalid)
   unsigned long long wait_ns = 0;   // limit of the TMA-staged pass's per-view waits (0: one second)
+  int sms = 0;                 // SMs of the device: the persistent z passes launch (resident CTAs per SM) x sms CTAs
   int stall = 0;               // test only: the compute warps' first wait is on a barrier nothing completes
 };
 

@@ -20,6 +20,8 @@
 // transposed split), so it needs two exchanges for a forward+inverse pair.
 #pragma once
 
+#include <algorithm>
+
 #include "pass_common.cuh"
 #include "zpass.cuh"
 
@@ -324,12 +326,17 @@ struct PassImpl {
     a.sel.nslots = nslots;
     if constexpr (ZW<L>::ok) {
       if (a.use_tma && (2 * a.nx) % ZW<L>::P == 0 && a.nz <= 256) {
-        k_zw<L><<<(2 * a.nx / ZW<L>::P) * (2 * a.ny), ZW<L>::NT, ZW<L>::smem, st>>>(a);
+        // persistent where the Green values live in registers: one wave of resident CTAs
+        const int ntiles = (2 * a.nx / ZW<L>::P) * (2 * a.ny);
+        const int grid = ZW<L>::GREG && a.sms > 0 ? std::min(ntiles, a.sms * ZW<L>::MINB) : ntiles;
+        k_zw<L><<<grid, ZW<L>::NT, ZW<L>::smem, st>>>(a);
         return;
       }
     } else if constexpr (ZG<L>::ok) {
       if (a.use_tma && (2 * a.nx) % ZG<L>::P == 0 && a.nz <= 256) {
-        k_zg<L><<<(2 * a.nx / ZG<L>::P) * (2 * a.ny), ZG<L>::NT, ZG<L>::smem, st>>>(a);
+        const int ntiles = (2 * a.nx / ZG<L>::P) * (2 * a.ny);
+        const int grid = a.sms > 0 ? std::min(ntiles, a.sms * ZG<L>::MINB) : ntiles;
+        k_zg<L><<<grid, ZG<L>::NT, ZG<L>::smem, st>>>(a);
         return;
       }
     }

@@ -160,23 +160,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
   return ok != 0;
 }
-// Non-blocking test of phase `parity` (acquire semantics when it returns true, like try_wait).
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
-  return ok != 0;
-}
-// try_wait that lets the hardware suspend the thread for up to `hint_ns` while the phase is pending
-// (for a warp with nothing else to do: it then takes no issue slots while it waits).
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, unsigned parity, unsigned hint_ns) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns) : "memory");
-  return ok != 0;
-}
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
@@ -194,13 +177,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
 }
 // mbar_wait that also gives up as soon as another thread of the CTA has set *abort, or after
-// limit_ns; a wait that runs out sets *abort itself.  sleep_ns > 0: suspend between checks.
+// limit_ns; a wait that runs out sets *abort itself.
 __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, volatile int* abort,
-                                                unsigned long long limit_ns, unsigned sleep_ns = 0) {
+                                                unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
-    if (sleep_ns ? mbar_try_wait_sleep(bar, parity, sleep_ns) : mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
     if (global_ns() - t0 > limit_ns) {
       *abort = 1;
@@ -248,16 +231,16 @@ struct ZW {
   static constexpr int XP = pitch(imax(R1 * (R2 + 2), R2 * (R1 + 2)));
   static constexpr int TWA = R1 + 2, TWB = R2 + 2;                            // twiddle rows (16-byte aligned)
   static constexpr int NS = 4;                                                // view buffers (TMA pipeline depth)
-  // each thread's Green values stay in registers across the view loop where they fit (R2 <= 16);
-  // the Green tile is then dead once they are loaded, and the exchange area reuses it
+  // each thread's Green values stay in registers across a tile's views where they fit (R2 <= 16),
+  // loaded from the octant; there is then no Green tile in shared memory and the kernel is persistent
   static constexpr bool GREG = R2 <= 16;
   static constexpr size_t r16(size_t b) { return (b + 15) / 16 * 16; }       // every region 16-byte aligned
   static constexpr size_t stage_bytes = (size_t)NZ * P * sizeof(float2);
   static constexpr size_t g_bytes = r16((size_t)(NZ + 1) * GR * sizeof(float2));
   static constexpr size_t x_bytes = r16((size_t)P * XP * sizeof(float2));
-  static constexpr size_t off_g = NS * stage_bytes;
+  static constexpr size_t off_g = NS * stage_bytes;          // Green tile (only without GREG)
   static constexpr size_t off_x = GREG ? off_g : off_g + g_bytes;
-  static constexpr size_t off_twa = off_x + (GREG ? (g_bytes > x_bytes ? g_bytes : x_bytes) : x_bytes);
+  static constexpr size_t off_twa = off_x + x_bytes;
   static constexpr size_t off_twb = off_twa + r16((size_t)R2 * TWA * sizeof(float2));
   static constexpr size_t off_bar = off_twb + r16((size_t)R1 * TWB * sizeof(float2));
   static constexpr int NBAR = 2 * NS + 1;                                     // full[NS], done[NS], never
@@ -280,12 +263,35 @@ __device__ __forceinline__ void green_mul(float2 (&u)[R2], const float2* gc, int
   }
 }
 
+// Green values of one thread for one (ky, 16-column kx) tile, read from the stored octant: kz = t + R1 k2,
+// folded into [0, L/2] (Ghat is even in every axis); column kx = kx0 + c folded into [0, nx].
+template <int L, int R1, int R2>
+__device__ __forceinline__ void load_green(float2 (&g)[R2], const ZParams& a, int ky, int kx, int t) {
+  const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
+  const int fx = kx <= a.nx ? kx : 2 * a.nx - kx;
+  const float2* col = a.gocta + (size_t)fy * (a.nx + 1) + fx;
+  const size_t plane = (size_t)(a.ny + 1) * (a.nx + 1);
+#pragma unroll
+  for (int k2 = 0; k2 < R2; ++k2) {
+    const int kz = k2 < R2 / 2 ? t + R1 * k2 : L - R1 * k2 - t;
+    g[k2] = __ldg(col + (size_t)kz * plane);
+  }
+}
+
+// Persistent form: each CTA owns the tiles blockIdx.x, blockIdx.x + gridDim.x, ... and streams the
+// (tile, view) items of all of them through its view buffers, so the per-CTA set-up (barriers, the
+// active-view list, twiddles) is paid once per CTA rather than once per tile.  Where the Green values
+// fit in registers (R2 <= 16) each thread loads its next tile's values straight from the octant right
+// after its last Green multiply of the current tile; the loads complete while the inverse transform of
+// that view and the forward transform of the next one run.  Longer splits (L = 384) keep one tile per
+// CTA and the Green tile in shared memory.
 template <int L>
 __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_constant__ ZParams a) {
   using W = ZW<L>;
   constexpr int R1 = W::R1, R2 = W::R2, P = W::P, NZ = W::NZ, CPW = W::CPW, T = W::T, NW = W::NW;
   static_assert(W::ok, "k_zw needs T | 32");
   static_assert(R1 % 2 == 0 && R2 % 2 == 0 && W::XP % 2 == 0, "16-byte exchange reads need even rows");
+  constexpr bool GREG = W::GREG;
   extern __shared__ __align__(16) unsigned char zw_raw[];
   const unsigned raw = smem_addr(zw_raw);
   unsigned char* base = zw_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -295,7 +301,7 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   float2* twa = reinterpret_cast<float2*>(base + W::off_twa);
   float2* twb = reinterpret_cast<float2*>(base + W::off_twb);
   constexpr int NS = W::NS;
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);   // [NS]: a view's tile has landed
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);   // [NS]: an item's tile has landed
   uint64_t* done = full + NS;                                         // [NS]: the compute warps are done with it
   uint64_t* never = done + NS;                                        // no thread arrives on it (stall test)
   __shared__ int s_list[kMaxLaunchSlots];
@@ -305,13 +311,21 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   if (nact == 0) return;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int ncont = 2 * a.nx;
-  const int tiles_c = ncont / P;
-  const int ky = blockIdx.x / tiles_c;
-  const int kx0 = (blockIdx.x % tiles_c) * P;
+  const int tiles_c = 2 * a.nx / P;
+  const int ntiles = tiles_c * 2 * a.ny;
+  // tiles of this CTA: blockIdx.x + k gridDim.x, k < ntl; items i = k nact + view
+  const int ntl = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int nitems = ntl * nact;
   const bool producer = warp == NW;
   // per-view wait limit (read from the parameter space where it is used, not held in a register)
 #define LS_ZW_LIMIT (a.wait_ns ? a.wait_ns : 1000000000ull)
+  // TMA coordinates of item i: (2 kx0 floats, ky, 0, slot)
+  auto item_load = [&](int i, int buf) {
+    const int j = (int)blockIdx.x + (i / nact) * (int)gridDim.x;
+    mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
+    tma_load_4d(stage + (size_t)buf * NZ * P, &a.tmap, &full[buf], 2 * (j % tiles_c) * P, j / tiles_c, 0,
+                a.slot0 + active_slot(s_list[i % nact]));
+  };
   if (producer && lane == 0) {
     s_abort = 0;
     for (int k = 0; k < NS; ++k) {
@@ -320,17 +334,17 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
     }
     mbar_init(never, 1);
     mbar_init_fence();
-    for (int k = 0; k < NS && k < nact; ++k) {
-      mbar_expect_tx(&full[k], (unsigned)W::stage_bytes);
-      tma_load_4d(stage + (size_t)k * NZ * P, &a.tmap, &full[k], 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[k]));
-    }
+    for (int k = 0; k < NS && k < nitems; ++k) item_load(k, k);
   }
-  // Ghat tile with kz folded into [0, NZ] (Ghat is even in every axis), and the stage twiddles
-  const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
-  for (int i = tid; i < (NZ + 1) * P; i += W::NT) {
-    const int kz = i / P, cc = i % P, kx = kx0 + cc;
-    const int fx = kx <= a.nx ? kx : ncont - kx;
-    gs[kz * W::GR + cc] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+  if constexpr (!GREG) {
+    // one tile per CTA (the launch has one CTA per tile): its Green tile, kz folded into [0, NZ]
+    const int ky = blockIdx.x / tiles_c, kx0 = (blockIdx.x % tiles_c) * P;
+    const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
+    for (int i = tid; i < (NZ + 1) * P; i += W::NT) {
+      const int kz = i / P, cc = i % P, kx = kx0 + cc;
+      const int fx = kx <= a.nx ? kx : 2 * a.nx - kx;
+      gs[kz * W::GR + cc] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+    }
   }
   for (int i = tid; i < R1 * R2; i += W::NT) {
     twa[(i / R1) * W::TWA + i % R1] = __ldg(a.zwa + i);
@@ -338,62 +352,57 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   }
   __syncthreads();
   if (producer) {
-    // producer: after the compute warps release a view's buffer, store it and refill it with the
-    // view NS ahead
+    // producer: after the compute warps release an item's buffer, store it and refill it with the
+    // item NS ahead
     if (lane != 0) return;
-    int iv = 0;
-    for (; iv < nact; ++iv) {
-      const int buf = iv % NS;
-      if (!mbar_wait_abort(&done[buf], (unsigned)(iv / NS) & 1u, &s_abort, LS_ZW_LIMIT, 2000u)) break;
-      float2* sb = stage + (size_t)buf * NZ * P;
-      tma_store_4d(&a.tmap, sb, 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[iv]));
+    int i = 0;
+    for (; i < nitems; ++i) {
+      const int buf = i % NS;
+      if (!mbar_wait_abort(&done[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZW_LIMIT)) break;
+      const int j = (int)blockIdx.x + (i / nact) * (int)gridDim.x;
+      tma_store_4d(&a.tmap, stage + (size_t)buf * NZ * P, 2 * (j % tiles_c) * P, j / tiles_c, 0,
+                   a.slot0 + active_slot(s_list[i % nact]));
       bulk_commit();
-      if (iv + NS < nact) {
+      if (i + NS < nitems) {
         bulk_wait_read_all();   // the store has read the buffer
-        mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
-        tma_load_4d(sb, &a.tmap, &full[buf], 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[iv + NS]));
+        item_load(i + NS, buf);
       }
     }
     bulk_wait_read_all();
-    if (iv < nact) {
-      // gave up at view iv: flag it, and give the loads still in flight into this CTA's buffers
-      // (views iv .. iv + NS - 1, all issued) a bounded time to land (one second each, whatever
+    if (i < nitems) {
+      // gave up at item i: flag it, and give the loads still in flight into this CTA's buffers
+      // (items i .. i + NS - 1, all issued) a bounded time to land (one second each, whatever
       // the per-view limit)
       atomicExch(a.err, 1);
-      for (int j = iv; j < iv + NS && j < nact; ++j) mbar_wait(&full[j % NS], (unsigned)(j / NS) & 1u);
+      for (int k = i; k < i + NS && k < nitems; ++k) mbar_wait(&full[k % NS], (unsigned)(k / NS) & 1u);
     }
     return;
   }
   // compute warps: each owns CPW whole columns (lane = t * CPW + column)
   const int t = lane / CPW;
   const int c = warp * CPW + lane % CPW;
+  const bool stage2_thread = R1 == T || t < R1;   // threads with a stage-2 (and Green) share
   float2* xc = xs + c * W::XP;
   const float2* gc = gs + c;
   // byte offset of (z = t + R2 j, c) in a tile: row base for j = 0, plus j R2 rows
   const unsigned rb = swz128(t, c);
-  // this thread's Green values (kz = t + R1 k2, the same for every view) stay in registers where
-  // they fit (R2 <= 16); longer splits read them from the shared tile for every view
-  constexpr bool GREG = W::GREG;
+  // this thread's Green values (kz = t + R1 k2, the same for every view of a tile) in registers
+  // where they fit (R2 <= 16); longer splits read them from the shared tile for every view
   float2 g[GREG ? R2 : 1];
+  if constexpr (GREG) {
+    if (stage2_thread) load_green<L, R1, R2>(g, a, blockIdx.x / tiles_c, (blockIdx.x % tiles_c) * P + c, t);
+    else
 #pragma unroll
-  for (int k2 = 0; k2 < (GREG ? R2 : 1); ++k2)
-    g[k2] = (GREG && (R1 == T || t < R1))
-                ? (k2 < R2 / 2 ? gc[(t + R1 * k2) * W::GR] : gc[(L - R1 * k2 - t) * W::GR])
-                : make_float2(0.f, 0.f);
-  // the exchange area overlays the Green tile: every compute warp has its values before any writes
-  if constexpr (GREG) asm volatile("bar.sync 1, %0;\n" ::"r"(NW * 32) : "memory");
-  bool next_ready = false;   // this view's tile was seen complete by a test during the previous view
+      for (int k2 = 0; k2 < R2; ++k2) g[k2] = make_float2(0.f, 0.f);
+  }
 #pragma unroll 1
-  for (int iv = 0; iv < nact; ++iv) {
-    const int buf = iv % NS;
-    const bool ok = (a.stall && iv == 0) ? mbar_wait_abort(never, 0u, &s_abort, LS_ZW_LIMIT)
-                    : next_ready         ? true
-                                         : mbar_wait_abort(&full[buf], (unsigned)(iv / NS) & 1u, &s_abort, LS_ZW_LIMIT);
+  for (int i = 0; i < nitems; ++i) {
+    const int buf = i % NS;
+    const int iv = i % nact;
+    const bool ok = (a.stall && i == 0) ? mbar_wait_abort(never, 0u, &s_abort, LS_ZW_LIMIT)
+                                        : mbar_wait_abort(&full[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZW_LIMIT);
     if (!__all_sync(0xffffffffu, ok)) break;
-    // the next view's barrier is tested now, without blocking; its answer is used at the top of the
-    // next iteration, so the test's latency overlaps this view's transforms
-    next_ready = iv + 1 < nact && mbar_test_wait(&full[(iv + 1) % NS], (unsigned)((iv + 1) / NS) & 1u);
-    count_run(a.sel);
+    if (i < nact) count_run(a.sel);   // each view once per launch (by the first tile of CTA 0)
     unsigned char* sb = reinterpret_cast<unsigned char*>(stage + (size_t)buf * NZ * P);
     float2 u[R2];
     if (R2 == T || t < R2) {
@@ -416,12 +425,12 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
       for (int k1 = 0; k1 < R1; ++k1) xc[k1 * (R2 + 2) + t] = v[k1];
     }
     __syncwarp();
-    if (R1 == T || t < R1) {
+    if (stage2_thread) {
 #pragma unroll
-      for (int i = 0; i < R2 / 2; ++i) {
-        const float4 q = *reinterpret_cast<const float4*>(xc + t * (R2 + 2) + 2 * i);
-        u[2 * i] = make_float2(q.x, q.y);
-        u[2 * i + 1] = make_float2(q.z, q.w);
+      for (int q = 0; q < R2 / 2; ++q) {
+        const float4 x = *reinterpret_cast<const float4*>(xc + t * (R2 + 2) + 2 * q);
+        u[2 * q] = make_float2(x.x, x.y);
+        u[2 * q + 1] = make_float2(x.z, x.w);
       }
       Dft<R2, -1>::run(u);
       // the adjoint flag is read from the active list where it is used (not held across the stages)
@@ -433,6 +442,12 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
         } else {
 #pragma unroll
           for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmul(u[k2], g[k2]);
+        }
+        // last view of this tile: the next tile's Green values, in flight during the rest of this
+        // view and the forward transform of the next item
+        if (iv == nact - 1 && i + 1 < nitems) {
+          const int j = (int)blockIdx.x + (i / nact + 1) * (int)gridDim.x;
+          load_green<L, R1, R2>(g, a, j / tiles_c, (j % tiles_c) * P + c, t);
         }
       } else if (adj) {
         green_mul<true, R1, R2, L, W::GR>(u, gc, t);
@@ -450,7 +465,7 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
       }
     }
     __syncwarp();
-    if (R1 == T || t < R1) {
+    if (stage2_thread) {
 #pragma unroll
       for (int j1 = 0; j1 < R2; ++j1) xc[j1 * (R1 + 2) + t] = u[j1];
     }
@@ -458,10 +473,10 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
     if (R2 == T || t < R2) {
       float2 w[R1];
 #pragma unroll
-      for (int i = 0; i < R1 / 2; ++i) {
-        const float4 q = *reinterpret_cast<const float4*>(xc + t * (R1 + 2) + 2 * i);
-        w[2 * i] = make_float2(q.x, q.y);
-        w[2 * i + 1] = make_float2(q.z, q.w);
+      for (int q = 0; q < R1 / 2; ++q) {
+        const float4 x = *reinterpret_cast<const float4*>(xc + t * (R1 + 2) + 2 * q);
+        w[2 * q] = make_float2(x.x, x.y);
+        w[2 * q + 1] = make_float2(x.z, x.w);
       }
       Dft<R1, +1, R1, R1 / 2>::run(w);
       // outputs z = t + R2 j2 (j2 < R1/2: z < nz), in place
@@ -509,16 +524,12 @@ struct ZG {
   static constexpr int RA = R2 + 2, RB = R1 + 2;
   static constexpr int pitch(int n) { return n + ((2 - n % 16) % 16 + 16) % 16; }
   static constexpr int XP = pitch(imax(R1 * RA, R2 * RB));
-  // Green rows [kz][P + 8]: the two rows of a half-warp's reads are 8 words apart
-  static constexpr int GR = P + 8;
   static constexpr int TWA = R1 + 2, TWB = R2 + 2;
   static constexpr size_t r16(size_t b) { return (b + 15) / 16 * 16; }
   static constexpr size_t stage_bytes = (size_t)NZ * P * sizeof(float2);
-  static constexpr size_t g_bytes = r16((size_t)(NZ + 1) * GR * sizeof(float2));
   static constexpr size_t x_bytes = r16((size_t)P * XP * sizeof(float2));
-  static constexpr size_t off_g = NS * stage_bytes;   // the Green tile and the exchange area overlay
-  static constexpr size_t off_x = off_g;
-  static constexpr size_t off_twa = off_g + (g_bytes > x_bytes ? g_bytes : x_bytes);
+  static constexpr size_t off_x = NS * stage_bytes;   // (the Green values are loaded into registers)
+  static constexpr size_t off_twa = off_x + x_bytes;
   static constexpr size_t off_twb = off_twa + r16((size_t)R2 * TWA * sizeof(float2));
   static constexpr size_t off_bar = off_twb + r16((size_t)R1 * TWB * sizeof(float2));
   static constexpr int NBAR = 2 * NS + 1;                                     // full[NS], done[NS], never
@@ -558,17 +569,16 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
   using W = ZG<L>;
   constexpr int R1 = W::R1, R2 = W::R2, P = W::P, NZ = W::NZ, T = W::T, S1 = W::S1, CG = W::CG, WG = W::WG,
                 NW = W::NW, NS = W::NS, RA = W::RA, RB = W::RB;
-  static_assert(W::ok && CG * T == 32 * WG && R2 % T == 0, "k_zg split");
+  static_assert(W::ok && CG * T == 32 * WG && R2 % T == 0 && R1 == T, "k_zg split");
   static_assert(R1 % 2 == 0 && R2 % 2 == 0 && W::XP % 2 == 0, "16-byte exchange reads need even rows");
   extern __shared__ __align__(16) unsigned char zg_raw[];
   const unsigned raw = smem_addr(zg_raw);
   unsigned char* base = zg_raw + (((raw + 1023u) & ~1023u) - raw);
   float2* stage = reinterpret_cast<float2*>(base);
-  float2* gs = reinterpret_cast<float2*>(base + W::off_g);
   float2* xs = reinterpret_cast<float2*>(base + W::off_x);
   float2* twa = reinterpret_cast<float2*>(base + W::off_twa);
   float2* twb = reinterpret_cast<float2*>(base + W::off_twb);
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);   // [NS]: a view's tile has landed
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);   // [NS]: an item's tile has landed
   uint64_t* done = full + NS;                                         // [NS]: the compute warps are done with it
   uint64_t* never = done + NS;                                        // no thread arrives on it (stall test)
   __shared__ int s_list[kMaxLaunchSlots];
@@ -578,12 +588,19 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
   if (nact == 0) return;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int ncont = 2 * a.nx;
-  const int tiles_c = ncont / P;
-  const int ky = blockIdx.x / tiles_c;
-  const int kx0 = (blockIdx.x % tiles_c) * P;
+  const int tiles_c = 2 * a.nx / P;
+  const int ntiles = tiles_c * 2 * a.ny;
+  // persistent, as k_zw: tiles blockIdx.x + k gridDim.x, items i = k nact + view
+  const int ntl = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int nitems = ntl * nact;
   const bool producer = warp == NW;
 #define LS_ZG_LIMIT (a.wait_ns ? a.wait_ns : 1000000000ull)
+  auto item_load = [&](int i, int buf) {
+    const int j = (int)blockIdx.x + (i / nact) * (int)gridDim.x;
+    mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
+    tma_load_4d(stage + (size_t)buf * NZ * P, &a.tmap, &full[buf], 2 * (j % tiles_c) * P, j / tiles_c, 0,
+                a.slot0 + active_slot(s_list[i % nact]));
+  };
   if (producer && lane == 0) {
     s_abort = 0;
     for (int k = 0; k < NS; ++k) {
@@ -592,17 +609,7 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
     }
     mbar_init(never, 1);
     mbar_init_fence();
-    for (int k = 0; k < NS && k < nact; ++k) {
-      mbar_expect_tx(&full[k], (unsigned)W::stage_bytes);
-      tma_load_4d(stage + (size_t)k * NZ * P, &a.tmap, &full[k], 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[k]));
-    }
-  }
-  // Ghat tile with kz folded into [0, NZ] (Ghat is even in every axis), and the stage twiddles
-  const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
-  for (int i = tid; i < (NZ + 1) * P; i += W::NT) {
-    const int kz = i / P, cc = i % P, kx = kx0 + cc;
-    const int fx = kx <= a.nx ? kx : ncont - kx;
-    gs[kz * W::GR + cc] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+    for (int k = 0; k < NS && k < nitems; ++k) item_load(k, k);
   }
   for (int i = tid; i < R1 * R2; i += W::NT) {
     twa[(i / R1) * W::TWA + i % R1] = __ldg(a.zwa + i);
@@ -610,29 +617,27 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
   }
   __syncthreads();
   if (producer) {
-    // producer: after the compute warps release a view's buffer, store it and refill it with the
-    // view NS ahead
     if (lane != 0) return;
-    int iv = 0;
-    for (; iv < nact; ++iv) {
-      const int buf = iv % NS;
-      if (!mbar_wait_abort(&done[buf], (unsigned)(iv / NS) & 1u, &s_abort, LS_ZG_LIMIT, 2000u)) break;
-      float2* sb = stage + (size_t)buf * NZ * P;
-      tma_store_4d(&a.tmap, sb, 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[iv]));
+    int i = 0;
+    for (; i < nitems; ++i) {
+      const int buf = i % NS;
+      if (!mbar_wait_abort(&done[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZG_LIMIT)) break;
+      const int j = (int)blockIdx.x + (i / nact) * (int)gridDim.x;
+      tma_store_4d(&a.tmap, stage + (size_t)buf * NZ * P, 2 * (j % tiles_c) * P, j / tiles_c, 0,
+                   a.slot0 + active_slot(s_list[i % nact]));
       bulk_commit();
-      if (iv + NS < nact) {
+      if (i + NS < nitems) {
         bulk_wait_read_all();   // the store has read the buffer
-        mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
-        tma_load_4d(sb, &a.tmap, &full[buf], 2 * kx0, ky, 0, a.slot0 + active_slot(s_list[iv + NS]));
+        item_load(i + NS, buf);
       }
     }
     bulk_wait_read_all();
-    if (iv < nact) {
-      // gave up at view iv: flag it, and give the loads still in flight into this CTA's buffers
-      // (views iv .. iv + NS - 1, all issued) a bounded time to land (one second each, whatever
+    if (i < nitems) {
+      // gave up at item i: flag it, and give the loads still in flight into this CTA's buffers
+      // (items i .. i + NS - 1, all issued) a bounded time to land (one second each, whatever
       // the per-view limit)
       atomicExch(a.err, 1);
-      for (int j = iv; j < iv + NS && j < nact; ++j) mbar_wait(&full[j % NS], (unsigned)(j / NS) & 1u);
+      for (int k = i; k < i + NS && k < nitems; ++k) mbar_wait(&full[k % NS], (unsigned)(k / NS) & 1u);
     }
     return;
   }
@@ -642,24 +647,18 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
   const int t = g / CG, c = g % CG;
   const int cc = gi * CG + c;
   float2* xc = xs + cc * W::XP;
-  const float2* gc = gs + cc;
-  // this thread's Green values (kz = t + R1 k2, the same for every view) in registers
+  // this thread's Green values (kz = t + R1 k2) for the current tile, in registers
   float2 gr[R2];
-#pragma unroll
-  for (int k2 = 0; k2 < R2; ++k2) gr[k2] = k2 < R2 / 2 ? gc[(t + R1 * k2) * W::GR] : gc[(L - R1 * k2 - t) * W::GR];
-  // the exchange area overlays the Green tile: every compute warp has its values before any writes
-  named_sync<1, NW * 32>();
-  bool next_ready = false;
+  load_green<L, R1, R2>(gr, a, blockIdx.x / tiles_c, (blockIdx.x % tiles_c) * P + cc, t);
 #pragma unroll 1
-  for (int iv = 0; iv < nact; ++iv) {
-    const int buf = iv % NS;
-    const bool ok = (a.stall && iv == 0) ? mbar_wait_abort(never, 0u, &s_abort, LS_ZG_LIMIT)
-                    : next_ready         ? true
-                                         : mbar_wait_abort(&full[buf], (unsigned)(iv / NS) & 1u, &s_abort, LS_ZG_LIMIT);
-    // the group agrees (this is also the barrier that frees the exchange area of the previous view)
+  for (int i = 0; i < nitems; ++i) {
+    const int buf = i % NS;
+    const int iv = i % nact;
+    const bool ok = (a.stall && i == 0) ? mbar_wait_abort(never, 0u, &s_abort, LS_ZG_LIMIT)
+                                        : mbar_wait_abort(&full[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZG_LIMIT);
+    // the group agrees (this is also the barrier that frees the exchange area of the previous item)
     if (!group_all<W::NGRP, WG * 32>(gi, ok)) break;
-    next_ready = iv + 1 < nact && mbar_test_wait(&full[(iv + 1) % NS], (unsigned)((iv + 1) / NS) & 1u);
-    count_run(a.sel);
+    if (i < nact) count_run(a.sel);   // each view once per launch (by the first tile of CTA 0)
     unsigned char* sb = reinterpret_cast<unsigned char*>(stage + (size_t)buf * NZ * P);
     // forward stage 1: sub-transforms n2 = t + T s, inputs z = R2 n1 + n2 (n1 < R1/2: z < nz)
 #pragma unroll
@@ -685,10 +684,10 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
     // forward stage 2 (thread t = k1), Green multiply, inverse stage 1 (transposed split)
     float2 u[R2];
 #pragma unroll
-    for (int i = 0; i < R2 / 2; ++i) {
-      const float4 q = *reinterpret_cast<const float4*>(xc + t * RA + 2 * i);
-      u[2 * i] = make_float2(q.x, q.y);
-      u[2 * i + 1] = make_float2(q.z, q.w);
+    for (int q = 0; q < R2 / 2; ++q) {
+      const float4 x = *reinterpret_cast<const float4*>(xc + t * RA + 2 * q);
+      u[2 * q] = make_float2(x.x, x.y);
+      u[2 * q + 1] = make_float2(x.z, x.w);
     }
     Dft<R2, -1>::run(u);
     if (active_adj(s_list[iv])) {
@@ -697,6 +696,11 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
     } else {
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmul(u[k2], gr[k2]);
+    }
+    if (iv == nact - 1 && i + 1 < nitems) {
+      // last view of this tile: the next tile's Green values, in flight while the transforms run
+      const int j = (int)blockIdx.x + (i / nact + 1) * (int)gridDim.x;
+      load_green<L, R1, R2>(gr, a, j / tiles_c, (j % tiles_c) * P + cc, t);
     }
     Dft<R2, +1>::run(u);
     {
@@ -718,10 +722,10 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
       const int j1 = t + T * s;
       float2 w[R1];
 #pragma unroll
-      for (int i = 0; i < R1 / 2; ++i) {
-        const float4 q = *reinterpret_cast<const float4*>(xc + j1 * RB + 2 * i);
-        w[2 * i] = make_float2(q.x, q.y);
-        w[2 * i + 1] = make_float2(q.z, q.w);
+      for (int q = 0; q < R1 / 2; ++q) {
+        const float4 x = *reinterpret_cast<const float4*>(xc + j1 * RB + 2 * q);
+        w[2 * q] = make_float2(x.x, x.y);
+        w[2 * q + 1] = make_float2(x.z, x.w);
       }
       Dft<R1, +1, R1, R1 / 2>::run(w);
 #pragma unroll

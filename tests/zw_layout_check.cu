@@ -28,7 +28,7 @@ void check() {
   // values live in registers
   REQUIRE(W::off_g >= (size_t)W::NS * W::stage_bytes, L);
   REQUIRE(W::off_twa >= W::off_x + W::x_bytes, L);
-  REQUIRE(W::GREG ? W::off_twa >= W::off_g + W::g_bytes : W::off_x >= W::off_g + W::g_bytes, L);
+  REQUIRE(W::GREG || W::off_x >= W::off_g + W::g_bytes, L);   // Green tile only without GREG
   REQUIRE(W::off_twb >= W::off_twa + (size_t)W::R2 * W::TWA * sizeof(float2), L);
   REQUIRE(W::off_bar >= W::off_twb + (size_t)W::R1 * W::TWB * sizeof(float2), L);
   REQUIRE(W::NBAR == 2 * W::NS + 1 && W::smem >= W::off_bar + W::NBAR * sizeof(uint64_t) + 1023, L);
@@ -54,16 +54,15 @@ void check_groups() {
   constexpr size_t sm_capacity = 228 * 1024, per_cta_max = 227 * 1024, reserved_per_cta = 1024;
   REQUIRE(W::CG * W::T == 32 * W::WG && W::NGRP * W::CG == W::P && W::R2 % W::T == 0 && W::R1 == W::T, L);
   REQUIRE(W::stage_bytes % 1024 == 0, L);
-  REQUIRE(W::off_g % 16 == 0 && W::off_twa % 16 == 0 && W::off_twb % 16 == 0 && W::off_bar % 16 == 0, L);
-  REQUIRE(W::off_g >= (size_t)W::NS * W::stage_bytes, L);
-  REQUIRE(W::off_twa >= W::off_g + W::g_bytes && W::off_twa >= W::off_x + W::x_bytes, L);
+  REQUIRE(W::off_x % 16 == 0 && W::off_twa % 16 == 0 && W::off_twb % 16 == 0 && W::off_bar % 16 == 0, L);
+  REQUIRE(W::off_x >= (size_t)W::NS * W::stage_bytes, L);
+  REQUIRE(W::off_twa >= W::off_x + W::x_bytes, L);
   REQUIRE(W::off_twb >= W::off_twa + (size_t)W::R2 * W::TWA * sizeof(float2), L);
   REQUIRE(W::off_bar >= W::off_twb + (size_t)W::R1 * W::TWB * sizeof(float2), L);
   REQUIRE(W::NBAR == 2 * W::NS + 1 && W::smem >= W::off_bar + W::NBAR * sizeof(uint64_t) + 1023, L);
   REQUIRE(W::R1 * W::RA <= W::XP && W::R2 * W::RB <= W::XP, L);
   REQUIRE(W::XP % 16 == 2 && W::RA % 2 == 0 && W::RB % 2 == 0, L);
   REQUIRE((size_t)W::P * W::XP * sizeof(float2) <= W::x_bytes, L);
-  REQUIRE(W::GR % 16 == 8 && W::GR >= W::P, L);
   REQUIRE(W::smem <= per_cta_max, L);
   REQUIRE((size_t)W::MINB * (W::smem + static_smem + reserved_per_cta) <= sm_capacity, L);
   // every row read from the stage buffer and every output row lies in the tile
