@@ -101,6 +101,10 @@ typedef struct {
   double matvec_us_per_view;  /* batched operator application with the chosen variants, per view (µs)      */
   double solve_ms;            /* forward solve of the tuning batch with the chosen variants (ms)            */
   int from_cache;             /* 1: read from the LS_AUTOTUNE_CACHE file, nothing was timed                  */
+  int z_split;                /* 1: the TMA-staged z pass with its second radix split                          */
+  int strided_wide;           /* 1: the y passes with 32 pencils per CTA (else 16)                             */
+  int views_per_launch;       /* BiCGStab iteration launched over chunks of this many views (0: all at once)   */
+  int z_persist;              /* 1: the TMA-staged z pass persistent (one wave of CTAs streaming their tiles)  */
 } ls_tune;
 
 /* Fill *opt with the defaults listed above. */

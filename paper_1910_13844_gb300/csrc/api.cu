@@ -284,11 +284,13 @@ static StridedParams fy_base(ls_plan* P, SlotSel sel, const float2* src, size_t 
   a.src_plane = (size_t)P->ny * 2 * P->nx;        // FY input plane [ny][2nx]
   a.dst_plane = (size_t)2 * P->ny * 2 * P->nx;    // FY output plane [2ny][2nx]
   a.tw = P->tw_y;
+  a.wide = P->tune_strided_wide;
   return a;
 }
 
 static SlotSel counted(ls_plan* P, SlotSel s, int kind) {
-  s.runs = P->prof.runs_d ? P->prof.runs_d + kind : nullptr;
+  ls_plan* o = prof_owner(P);
+  s.runs = o->prof.runs_d ? o->prof.runs_d + kind : nullptr;
   return s;
 }
 
@@ -310,10 +312,12 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   z.gocta = P->gocta;
   z.twa = P->twa_z;
   z.twb = P->twb_z;
-  z.zwa = P->zwa_z;
-  z.zwb = P->zwb_z;
+  z.alt = P->tune_z_split && P->zwa2_z ? 1 : 0;
+  z.zwa = z.alt ? P->zwa2_z : P->zwa_z;
+  z.zwb = z.alt ? P->zwb2_z : P->zwb_z;
   z.wait_ns = (unsigned long long)P->inj_z_wait_ns;
   z.sms = P->sms;
+  z.persist = P->tune_z_persist;
   z.stall = P->inj_z_stall;
   timed(P, LS_K_Z, nslots, st, [&] { P->pz.z(z, nslots, st); });
   StridedParams iy = fy_base(P, counted(P, sel, LS_K_IY), e.a2, e.a2_stride, e.a1, e.a1_stride, P->nz);
@@ -420,6 +424,18 @@ void seq_iter(ls_plan* P, int nslots, cudaStream_t st) {
   }
 }
 
+void seq_iter_chunked(ls_plan* P, int nslots, cudaStream_t st) {
+  const int c = P->tune_views_per_launch;
+  if (c <= 0 || c >= nslots) {
+    seq_iter(P, nslots, st);
+    return;
+  }
+  for (int s0 = 0; s0 < nslots; s0 += c) {
+    ls_plan v = plan_slot_view(P, s0);
+    seq_iter(&v, std::min(c, nslots - s0), st);
+  }
+}
+
 // far[s] = G~ (f x_s) for the selected slots (eq. Gtild-1)
 void seq_far(ls_plan* P, int nslots, unsigned mask, cudaStream_t st) {
   Engine& e = P->eng;
@@ -507,7 +523,8 @@ int ensure_iter_graph(ls_plan* P, int nslots) {
   Engine& e = P->eng;
   // the captured launches carry the plan's launch variants: recapture when ls_autotune changed them
   const int variant = P->tune_z_tma | P->tune_ix_prefetch << 1 | P->tune_fx_views_fastest << 2 |
-                      (P->inj_z_stall || P->inj_z_wait_ns ? 1 << 3 : 0);
+                      (P->inj_z_stall || P->inj_z_wait_ns ? 1 << 3 : 0) | P->tune_z_split << 4 |
+                      P->tune_strided_wide << 5 | P->tune_z_persist << 6 | P->tune_views_per_launch << 7;
   if (e.iter_graph && e.iter_graph_slots == nslots && e.iter_graph_variant == variant) return LS_OK;
   if (e.iter_graph) {
     cudaGraphExecDestroy(e.iter_graph);
@@ -515,7 +532,7 @@ int ensure_iter_graph(ls_plan* P, int nslots) {
   }
   cudaGraph_t g;
   LS_CUDA_TRY(cudaStreamBeginCapture(e.cap_stream, cudaStreamCaptureModeThreadLocal));
-  seq_iter(P, nslots, e.cap_stream);
+  seq_iter_chunked(P, nslots, e.cap_stream);
   LS_CUDA_TRY(cudaStreamEndCapture(e.cap_stream, &g));
   cudaError_t err = cudaGraphInstantiate(&e.iter_graph, g, 0);
   cudaGraphDestroy(g);
@@ -532,6 +549,9 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   v.px = P->px; v.py = P->py; v.pz = P->pz;
   v.tw2_x = P->tw2_x; v.tw_y = P->tw_y;
   v.twa_z = P->twa_z; v.twb_z = P->twb_z; v.zwa_z = P->zwa_z; v.zwb_z = P->zwb_z;
+  v.zwa2_z = P->zwa2_z; v.zwb2_z = P->zwb2_z;
+  v.tune_z_split = P->tune_z_split; v.tune_strided_wide = P->tune_strided_wide; v.tune_z_persist = P->tune_z_persist;
+  v.tune_views_per_launch = P->tune_views_per_launch;
   v.gocta = P->gocta; v.k2hat = P->k2hat; v.p_built = P->p_built;
   v.device = P->device; v.sms = P->sms;
   v.tune_z_tma = P->tune_z_tma; v.tune_ix_prefetch = P->tune_ix_prefetch;
@@ -553,6 +573,7 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   w.slot0 = e.slot0 + s0;
   w.iter_graph = nullptr;
   w.cap_stream = nullptr;
+  v.prof_parent = const_cast<ls_plan*>(prof_owner(const_cast<ls_plan*>(P)));
   return v;
 }
 
@@ -563,6 +584,9 @@ ls_plan* plan_clone_shared(const ls_plan* P) {
   c->px = P->px; c->py = P->py; c->pz = P->pz;
   c->tw2_x = P->tw2_x; c->tw_y = P->tw_y;
   c->twa_z = P->twa_z; c->twb_z = P->twb_z; c->zwa_z = P->zwa_z; c->zwb_z = P->zwb_z;
+  c->zwa2_z = P->zwa2_z; c->zwb2_z = P->zwb2_z;
+  c->tune_z_split = P->tune_z_split; c->tune_strided_wide = P->tune_strided_wide; c->tune_z_persist = P->tune_z_persist;
+  c->tune_views_per_launch = P->tune_views_per_launch;
   c->gocta = P->gocta; c->k2hat = P->k2hat; c->p_built = P->p_built;
   c->device = P->device; c->sms = P->sms;
   c->tune_z_tma = P->tune_z_tma; c->tune_ix_prefetch = P->tune_ix_prefetch;
@@ -633,7 +657,7 @@ int engine_solve(ls_plan* P, int nslots, cudaStream_t st) {
       if (graphs) {
         LS_CUDA_TRY(cudaGraphLaunch(e.iter_graph, st));
       } else {
-        seq_iter(P, nslots, st);
+        seq_iter_chunked(P, nslots, st);
       }
     }
     LS_CUDA_TRY(cudaGetLastError());
@@ -862,6 +886,8 @@ int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel, c
   rc = make_twiddles(L[0], P->px.r1, P->px.r2, nullptr, &P->tw2_x);
   if (rc == LS_OK) rc = make_twiddles(L[1], P->py.r1, P->py.r2, &P->tw_y, nullptr);
   if (rc == LS_OK) rc = make_z_twiddles(L[2], P->pz.r1, P->pz.r2, &P->twa_z, &P->twb_z);
+  if (rc == LS_OK && P->pz.zalt_ok)
+    rc = make_z_twiddles(L[2], P->pz.zr1b, P->pz.zr2b, &P->zwa2_z, &P->zwb2_z);
   if (rc == LS_OK) {
     if (P->pz.zr1 == P->pz.r1) {
       P->zwa_z = P->twa_z;
@@ -909,6 +935,7 @@ void ls_plan_destroy(ls_plan* P) {
   if (P->owns_shared) {
     cudaFree(P->tw2_x); cudaFree(P->tw_y);
     if (P->zwa_z != P->twa_z) { cudaFree(P->zwa_z); cudaFree(P->zwb_z); }
+    cudaFree(P->zwa2_z); cudaFree(P->zwb2_z);
     cudaFree(P->twa_z); cudaFree(P->twb_z);
     cudaFree(P->gocta); cudaFree(P->k2hat);
   }

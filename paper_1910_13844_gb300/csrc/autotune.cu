@@ -1,10 +1,16 @@
 // Launch-variant autotuner.  For one plan and batch size it times the variants that the passes and
 // the solve loop can switch between at run time, on the plan's own grid and views:
 //   * the z pass: TMA-staged with warp-local exchanges, or cp.async-staged with CTA-wide exchanges;
+//   * the TMA-staged z pass's radix split: the default one or a second one (R1 x R2 transposed, or
+//     2 R1 x R2 / 2 where R1 = R2), where the length has one;
+//   * the TMA-staged z pass one CTA per tile, or persistent (one wave of CTAs, each streaming the
+//     views of several tiles);
+//   * FY / IY: 16 or 32 pencils per CTA;
 //   * IX: L2 prefetch of its epilogue operands at kernel start, or not;
 //   * FX: launch grid with the views fastest (shared potential rows from L2), or the rows fastest;
-//   * the solve loop: iterations between host reads of the convergence mask (2, 4, 8), and replay
-//     of the iteration from a captured CUDA graph or direct launches.
+//   * the solve loop: the views per launch of an iteration (all, or chunks of n/2, n/4 or 8 views,
+//     each chunk one launch per pass), iterations between host reads of the convergence mask
+//     (2, 4, 8), and replay of the iteration from a captured CUDA graph or direct launches.
 // Operator variants are timed on batched operator applications, the loop variants on forward solves
 // of plane-wave illuminations.  One knob is tuned at a time, in the order above, keeping the best
 // value of the earlier ones.  Results can be cached in a text file (LS_AUTOTUNE_CACHE) keyed by the
@@ -45,9 +51,16 @@ static bool cache_lookup(const std::string& key, ls_tune* t) {
   char k[256];
   ls_tune v;
   bool found = false;
-  while (fscanf(fp, "%255s %d %d %d %d %d %lf %lf", k, &v.z_tma, &v.ix_prefetch, &v.fx_views_fastest,
-                &v.check_every, &v.use_graphs, &v.matvec_us_per_view, &v.solve_ms) == 8)
-    if (key == k) { *t = v; found = true; }   // the last entry for a key wins
+  char line[512];
+  while (fgets(line, sizeof(line), fp)) {
+    if (sscanf(line, "%255s %d %d %d %d %d %lf %lf %d %d %d %d", k, &v.z_tma, &v.ix_prefetch, &v.fx_views_fastest,
+               &v.check_every, &v.use_graphs, &v.matvec_us_per_view, &v.solve_ms, &v.z_split, &v.strided_wide,
+               &v.views_per_launch, &v.z_persist) == 12 &&
+        key == k) {
+      *t = v;   // the last entry for a key wins
+      found = true;
+    }
+  }
   fclose(fp);
   return found;
 }
@@ -58,8 +71,9 @@ static void cache_store(const std::string& key, const ls_tune& t) {
   std::lock_guard<std::mutex> lock(g_cache_mu);
   FILE* fp = fopen(path, "a");
   if (!fp) return;
-  fprintf(fp, "%s %d %d %d %d %d %.9g %.9g\n", key.c_str(), t.z_tma, t.ix_prefetch, t.fx_views_fastest,
-          t.check_every, t.use_graphs, t.matvec_us_per_view, t.solve_ms);
+  fprintf(fp, "%s %d %d %d %d %d %.9g %.9g %d %d %d %d\n", key.c_str(), t.z_tma, t.ix_prefetch, t.fx_views_fastest,
+          t.check_every, t.use_graphs, t.matvec_us_per_view, t.solve_ms, t.z_split, t.strided_wide, t.views_per_launch,
+          t.z_persist);
   fclose(fp);
 }
 
@@ -69,6 +83,10 @@ static void apply(ls_plan* P, const ls_tune& t) {
   P->tune_fx_views_fastest = t.fx_views_fastest;
   P->opt.check_every = t.check_every;
   P->opt.use_graphs = t.use_graphs;
+  P->tune_z_split = t.z_split && P->zwa2_z ? 1 : 0;
+  P->tune_strided_wide = t.strided_wide;
+  P->tune_views_per_launch = t.views_per_launch;
+  P->tune_z_persist = t.z_persist;
 }
 
 // mean milliseconds of `reps` calls of fn after one untimed call; negative on error
@@ -103,6 +121,8 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   ls_tune best;
   if (cache_lookup(key, &best)) {
     if (!P->eng.a2_map_ok) best.z_tma = 0;
+    if (!P->zwa2_z) best.z_split = 0;
+    if (best.views_per_launch >= n_views) best.views_per_launch = 0;
     apply(P, best);
     best.from_cache = 1;
     if (out) *out = best;
@@ -136,6 +156,10 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   cur.fx_views_fastest = 1;
   cur.check_every = P->opt.check_every > 0 ? P->opt.check_every : 2;
   cur.use_graphs = 1;
+  cur.z_split = 0;
+  cur.strided_wide = 0;
+  cur.views_per_launch = 0;
+  cur.z_persist = 0;
   cur.from_cache = 0;
   auto matvec = [&] { return tune_matvec(P, f, n_views, st); };
   auto tune_op = [&](int* knob, int n_values, const int* values) -> double {
@@ -154,12 +178,32 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   static const int two[2] = {1, 0};
   double mv_ms = -1.0;
   if (e.a2_map_ok) mv_ms = tune_op(&cur.z_tma, 2, two);
+  if (e.a2_map_ok && cur.z_tma && P->zwa2_z) mv_ms = tune_op(&cur.z_split, 2, two);
+  if (e.a2_map_ok && cur.z_tma) mv_ms = tune_op(&cur.z_persist, 2, two);
+  mv_ms = tune_op(&cur.strided_wide, 2, two);
   mv_ms = tune_op(&cur.ix_prefetch, 2, two);
   mv_ms = tune_op(&cur.fx_views_fastest, 2, two);
   // solve loop: forward solves of the plane waves
   auto solve = [&] { return tune_forward(P, f, n_views, st); };
+  auto solve_views = solve;
   double sv_ms = -1.0;
   {
+    // views per launch of an iteration: all of them, or chunks of n/2, n/4 or 8 views
+    int cands[4] = {0, n_views / 2, n_views / 4, 8};
+    int best_c = 0;
+    double best_c_ms = -1.0;
+    for (int ci = 0; ci < 4; ++ci) {
+      const int cv = cands[ci];
+      if (ci > 0 && (cv < 1 || cv >= n_views)) continue;
+      bool seen = false;
+      for (int cj = 1; cj < ci; ++cj) seen = seen || cands[cj] == cv;
+      if (seen) continue;
+      cur.views_per_launch = cv;
+      apply(P, cur);
+      const double ms = time_ms(st, 1, solve_views);
+      if (ms > 0 && (best_c_ms < 0 || ms < best_c_ms)) { best_c_ms = ms; best_c = cv; }
+    }
+    cur.views_per_launch = best_c;
     static const int chunks[3] = {4, 2, 8};
     int best_v = cur.check_every;
     for (int c : chunks) {

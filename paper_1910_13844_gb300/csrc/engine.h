@@ -67,6 +67,7 @@ struct ls_plan {
   float2 *tw2_x = nullptr, *tw_y = nullptr;   // x-pass stage twiddles [k1*R2 + n2]; y-pass exp(-2 pi i j / L)
   float2 *twa_z = nullptr, *twb_z = nullptr;
   float2 *zwa_z = nullptr, *zwb_z = nullptr;   // z tables for the TMA-staged split (alias twa_z/twb_z if equal)
+  float2 *zwa2_z = nullptr, *zwb2_z = nullptr; // z tables for its second split (null if the length has none)
   float2* gocta = nullptr;
   float2* k2hat = nullptr;
   int p_built = 0;
@@ -76,6 +77,10 @@ struct ls_plan {
   int tune_z_tma = 1;           // TMA-staged z pass where available (else the cp.async-staged one)
   int tune_ix_prefetch = 1;     // IX asks L2 for its epilogue operands at kernel start
   int tune_fx_views_fastest = 0;  // FX grid with views fastest (else row blocks fastest)
+  int tune_z_split = 0;           // TMA-staged z pass with its second radix split
+  int tune_z_persist = 0;         // persistent TMA-staged z pass
+  int tune_strided_wide = 0;      // FY/IY with 32 pencils per CTA (else 16)
+  int tune_views_per_launch = 0;  // BiCGStab iteration launched over chunks of this many views (0: all)
   // test-only failure injection (ls_debug_inject); the defaults inject nothing
   int inj_zero_shadow_view = -1;  // this view's shadow residual is zeroed at the start of a solve
   long long inj_max_rounds = -1;  // host rounds a solve may take (-1: the normal bound)
@@ -89,6 +94,7 @@ struct ls_plan {
   int noalloc_rc = 0;
   lsgpu::Engine eng;
   lsgpu::Profiler prof;
+  ls_plan* prof_parent = nullptr;   // slot views time their launches in the viewed plan's profiler
 };
 
 namespace lsgpu {
@@ -103,6 +109,8 @@ int engine_solve(ls_plan* P, int nslots, cudaStream_t st);
 // Sequences of kernel launches (no synchronisation).
 void seq_resid(ls_plan* P, int nslots, cudaStream_t st);
 void seq_iter(ls_plan* P, int nslots, cudaStream_t st);
+// seq_iter over chunks of P->tune_views_per_launch slots (one launch per pass and chunk)
+void seq_iter_chunked(ls_plan* P, int nslots, cudaStream_t st);
 void seq_far(ls_plan* P, int nslots, unsigned mask, cudaStream_t st);
 void seq_far_adjoint(ls_plan* P, int nslots, const float2* const* r_dev_table, unsigned mask, cudaStream_t st);
 int engine_upload_ptrs(ls_plan* P, int table, const void* const* host_ptrs, int n, cudaStream_t st);
@@ -128,8 +136,10 @@ int noalloc_setup(void** addr);
 // Launch wrapper: when profiling is on, bracket the launch with an event pair.
 cudaEvent_t prof_event(ls_plan* P);
 void prof_resolve(ls_plan* P, bool wait);
+inline ls_plan* prof_owner(ls_plan* P) { return P->prof_parent ? P->prof_parent : P; }
 template <class F>
-inline void timed(ls_plan* P, int kind, int nslots, cudaStream_t st, F&& launch) {
+inline void timed(ls_plan* P0, int kind, int nslots, cudaStream_t st, F&& launch) {
+  ls_plan* P = prof_owner(P0);
   if (!P->prof.on) {
     launch();
     return;

@@ -48,6 +48,7 @@ struct StridedParams {
   float2* dst; size_t dst_stride;
   size_t src_plane, dst_plane; // elements between planes
   const float2* tw;            // tw[j] = exp(-2 pi i j / L)
+  int wide = 0;                // 32 pencils per CTA instead of 16 (autotuned)
 };
 
 struct ZParams {
@@ -65,6 +66,8 @@ struct ZParams {
   int* err;                    // set to 1 if a wait for a TMA copy gave up (the launch's output is invalid)
   unsigned long long wait_ns = 0;   // limit of the TMA-staged pass's per-view waits (0: one second)
   int sms = 0;                 // SMs of the device: the persistent z passes launch (resident CTAs per SM) x sms CTAs
+  int alt = 0;                 // TMA-staged z pass with the second split (zwa/zwb are that split's tables)
+  int persist = 0;             // persistent TMA-staged z pass (one wave of CTAs streaming their tiles' views)
   int stall = 0;               // test only: the compute warps' first wait is on a barrier nothing completes
 };
 

@@ -140,10 +140,11 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 6) k_fx(FxParams a) {
 
 // ------------------------------------------------------------------------- FY / IY
 // Pencils along a strided axis; tile = 16 consecutive entries of the contiguous axis.
-template <int L, int DIR>
-__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS) k_strided(StridedParams a) {
+// P = 16 or 32 pencils per CTA (P 8-byte entries of a row: 128 or 256 contiguous bytes per load).
+template <int L, int DIR, int P>
+__global__ void __launch_bounds__(Geo<L>::T * P) k_strided(StridedParams a) {
   using G = Geo<L>;
-  constexpr int R1 = G::R1, R2 = G::R2, P = G::PS;
+  constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
   const int slot = blockIdx.y;
   if (!slot_runs(a.sel, slot)) return;
@@ -299,6 +300,8 @@ struct PassLaunch {
   int pencils_per_cta_strided;
   int r1, r2;   // the split L = r1 * r2 of the two register stages (twiddle tables follow it)
   int zr1, zr2; // the split of the TMA-staged z pass
+  int zalt_ok;  // a second split of the TMA-staged z pass exists (autotuned)
+  int zr1b, zr2b;
 };
 
 template <int L>
@@ -313,48 +316,89 @@ struct PassImpl {
     dim3 blk(G::T, G::PC), grd((a.rows + G::PC - 1) / G::PC, nslots);
     k_ix<L><<<grd, blk, G::smem_contig, st>>>(a);
   }
-  static void fy(const StridedParams& a, int nslots, cudaStream_t st) {
-    dim3 blk(G::PS, G::T), grd(((a.ncont + G::PS - 1) / G::PS) * a.planes, nslots);
-    k_strided<L, -1><<<grd, blk, G::smem_strided, st>>>(a);
+  template <int DIR>
+  static void strided(const StridedParams& a, int nslots, cudaStream_t st) {
+    if (a.wide && G::T * 32 <= 1024) {
+      constexpr int W = G::T * 32 <= 1024 ? 32 : 16;
+      dim3 blk(W, G::T), grd(((a.ncont + W - 1) / W) * a.planes, nslots);
+      k_strided<L, DIR, W><<<grd, blk, (size_t)L * W * sizeof(float2), st>>>(a);
+    } else {
+      dim3 blk(G::PS, G::T), grd(((a.ncont + G::PS - 1) / G::PS) * a.planes, nslots);
+      k_strided<L, DIR, G::PS><<<grd, blk, G::smem_strided, st>>>(a);
+    }
   }
-  static void iy(const StridedParams& a, int nslots, cudaStream_t st) {
-    dim3 blk(G::PS, G::T), grd(((a.ncont + G::PS - 1) / G::PS) * a.planes, nslots);
-    k_strided<L, +1><<<grd, blk, G::smem_strided, st>>>(a);
-  }
+  static void fy(const StridedParams& a, int nslots, cudaStream_t st) { strided<-1>(a, nslots, st); }
+  static void iy(const StridedParams& a, int nslots, cudaStream_t st) { strided<+1>(a, nslots, st); }
   static void z(const ZParams& a0, int nslots, cudaStream_t st) {
     ZParams a = a0;
     a.sel.nslots = nslots;
+    if constexpr (ZW<L, true>::ok) {
+      if (a.alt && a.use_tma && (2 * a.nx) % ZW<L, true>::P == 0 && a.nz <= 256) {
+        launch_zw<true>(a, st);
+        return;
+      }
+    }
     if constexpr (ZW<L>::ok) {
       if (a.use_tma && (2 * a.nx) % ZW<L>::P == 0 && a.nz <= 256) {
-        // persistent where the Green values live in registers: one wave of resident CTAs
-        const int ntiles = (2 * a.nx / ZW<L>::P) * (2 * a.ny);
-        const int grid = ZW<L>::GREG && a.sms > 0 ? std::min(ntiles, a.sms * ZW<L>::MINB) : ntiles;
-        k_zw<L><<<grid, ZW<L>::NT, ZW<L>::smem, st>>>(a);
+        launch_zw<false>(a, st);
         return;
       }
     } else if constexpr (ZG<L>::ok) {
       if (a.use_tma && (2 * a.nx) % ZG<L>::P == 0 && a.nz <= 256) {
         const int ntiles = (2 * a.nx / ZG<L>::P) * (2 * a.ny);
-        const int grid = a.sms > 0 ? std::min(ntiles, a.sms * ZG<L>::MINB) : ntiles;
-        k_zg<L><<<grid, ZG<L>::NT, ZG<L>::smem, st>>>(a);
+        if (a.persist && a.sms > 0)
+          k_zg<L, true><<<std::min(ntiles, a.sms * ZG<L>::MINB), ZG<L>::NT, ZG<L>::smem, st>>>(a);
+        else
+          k_zg<L, false><<<ntiles, ZG<L>::NT, ZG<L>::smem, st>>>(a);
         return;
       }
     }
     dim3 blk(G::PS, G::T), grd(((2 * a.nx + G::PS - 1) / G::PS) * (2 * a.ny));
     k_z<L><<<grd, blk, G::smem_z, st>>>(a);
   }
+  // persistent where the Green values live in registers: one wave of resident CTAs
+  template <bool ALT>
+  static void launch_zw(const ZParams& a, cudaStream_t st) {
+    using W = ZW<L, ALT>;
+    const int ntiles = (2 * a.nx / W::P) * (2 * a.ny);
+    if constexpr (W::GREG) {
+      if (a.persist && a.sms > 0) {
+        k_zw<L, ALT, true><<<std::min(ntiles, a.sms * W::MINB), W::NT, W::smem, st>>>(a);
+        return;
+      }
+    }
+    k_zw<L, ALT, false><<<ntiles, W::NT, W::smem, st>>>(a);
+  }
+  template <bool ALT>
+  static cudaError_t setup_zw() {
+    using W = ZW<L, ALT>;
+    cudaError_t e = cudaFuncSetAttribute(k_zw<L, ALT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W::smem);
+    if constexpr (W::GREG)
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_zw<L, ALT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W::smem);
+    return e;
+  }
   static cudaError_t setup() {
     cudaError_t e = cudaSuccess;
     {
       e = cudaFuncSetAttribute(k_fx<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ix<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, -1, G::PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, +1, G::PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
+      if constexpr (G::T * 32 <= 1024) {
+        constexpr int sw = (int)(L * 32 * sizeof(float2));
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, -1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, +1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw);
+      }
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_z);
       if constexpr (ZW<L>::ok)
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zw<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZW<L>::smem);
-      if constexpr (ZG<L>::ok)
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zg<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZG<L>::smem);
+        if (e == cudaSuccess) e = setup_zw<false>();
+      if constexpr (ZW<L, true>::ok)
+        if (e == cudaSuccess) e = setup_zw<true>();
+      if constexpr (ZG<L>::ok) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zg<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZG<L>::smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zg<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZG<L>::smem);
+      }
     }
     return e;
   }
@@ -367,6 +411,9 @@ struct PassImpl {
     t.r2 = G::R2;
     t.zr1 = ZRadix<L>::R1;
     t.zr2 = ZRadix<L>::R2;
+    t.zalt_ok = ZW<L, true>::ok ? 1 : 0;
+    t.zr1b = ZRadixAlt<L>::R1;
+    t.zr2b = ZRadixAlt<L>::R2;
     return t;
   }
 };

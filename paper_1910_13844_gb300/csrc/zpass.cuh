@@ -211,12 +211,20 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 template <int L> struct ZRadix { static constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2; };
 template <> struct ZRadix<96>  { static constexpr int R1 = 16, R2 = 6;  };
 template <> struct ZRadix<384> { static constexpr int R1 = 12, R2 = 32; };
+// A second split of the same length for the autotuner: the transposed one where R1 != R2, else
+// (2 R1, R2 / 2) (both factors even, thread count max(R1, R2) dividing 32 where it is usable)
+template <int L> struct ZRadixAlt {
+  static constexpr int R1 = ZRadix<L>::R1 != ZRadix<L>::R2 ? ZRadix<L>::R2 : 2 * ZRadix<L>::R1;
+  static constexpr int R2 = ZRadix<L>::R1 != ZRadix<L>::R2 ? ZRadix<L>::R1 : ZRadix<L>::R2 / 2;
+};
+template <int L, bool ALT> struct ZSplit { static constexpr int R1 = ZRadix<L>::R1, R2 = ZRadix<L>::R2; };
+template <int L> struct ZSplit<L, true> { static constexpr int R1 = ZRadixAlt<L>::R1, R2 = ZRadixAlt<L>::R2; };
 
-template <int L>
+template <int L, bool ALT = false>
 struct ZW {
-  static constexpr int R1 = ZRadix<L>::R1, R2 = ZRadix<L>::R2;
+  static constexpr int R1 = ZSplit<L, ALT>::R1, R2 = ZSplit<L, ALT>::R2;
   static constexpr int T = imax(R1, R2);
-  static constexpr bool ok = (32 % T) == 0;
+  static constexpr bool ok = (32 % T) == 0 && R1 % 2 == 0 && R2 % 2 == 0 && R1 >= 2 && R2 >= 2;
   static constexpr int CPW = ok ? 32 / T : 1;   // whole columns per warp (lane = t * CPW + column)
   static constexpr int P = 16;                  // columns per CTA: one 128-byte TMA row
   static constexpr int NW = P / CPW;             // compute warps
@@ -231,16 +239,17 @@ struct ZW {
   static constexpr int XP = pitch(imax(R1 * (R2 + 2), R2 * (R1 + 2)));
   static constexpr int TWA = R1 + 2, TWB = R2 + 2;                            // twiddle rows (16-byte aligned)
   static constexpr int NS = 4;                                                // view buffers (TMA pipeline depth)
-  // each thread's Green values stay in registers across a tile's views where they fit (R2 <= 16),
-  // loaded from the octant; there is then no Green tile in shared memory and the kernel is persistent
+  // each thread's Green values stay in registers across a tile's views where they fit (R2 <= 16); the
+  // Green tile is then dead once they are loaded and the exchange area reuses it, and the kernel can
+  // also run persistent (Green values loaded per tile from the octant)
   static constexpr bool GREG = R2 <= 16;
   static constexpr size_t r16(size_t b) { return (b + 15) / 16 * 16; }       // every region 16-byte aligned
   static constexpr size_t stage_bytes = (size_t)NZ * P * sizeof(float2);
   static constexpr size_t g_bytes = r16((size_t)(NZ + 1) * GR * sizeof(float2));
   static constexpr size_t x_bytes = r16((size_t)P * XP * sizeof(float2));
-  static constexpr size_t off_g = NS * stage_bytes;          // Green tile (only without GREG)
-  static constexpr size_t off_x = GREG ? off_g : off_g + g_bytes;
-  static constexpr size_t off_twa = off_x + x_bytes;
+  static constexpr size_t off_g = NS * stage_bytes;
+  static constexpr size_t off_x = GREG ? off_g : off_g + g_bytes;   // with GREG the exchange overlays the Green tile
+  static constexpr size_t off_twa = off_x + (GREG ? (g_bytes > x_bytes ? g_bytes : x_bytes) : x_bytes);
   static constexpr size_t off_twb = off_twa + r16((size_t)R2 * TWA * sizeof(float2));
   static constexpr size_t off_bar = off_twb + r16((size_t)R1 * TWB * sizeof(float2));
   static constexpr int NBAR = 2 * NS + 1;                                     // full[NS], done[NS], never
@@ -278,16 +287,17 @@ __device__ __forceinline__ void load_green(float2 (&g)[R2], const ZParams& a, in
   }
 }
 
-// Persistent form: each CTA owns the tiles blockIdx.x, blockIdx.x + gridDim.x, ... and streams the
-// (tile, view) items of all of them through its view buffers, so the per-CTA set-up (barriers, the
-// active-view list, twiddles) is paid once per CTA rather than once per tile.  Where the Green values
-// fit in registers (R2 <= 16) each thread loads its next tile's values straight from the octant right
-// after its last Green multiply of the current tile; the loads complete while the inverse transform of
-// that view and the forward transform of the next one run.  Longer splits (L = 384) keep one tile per
-// CTA and the Green tile in shared memory.
-template <int L>
-__global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_constant__ ZParams a) {
-  using W = ZW<L>;
+// One CTA per tile (PERSIST = false), or persistent (PERSIST = true, Green values in registers only):
+// each CTA owns the tiles blockIdx.x, blockIdx.x + gridDim.x, ... and streams the (tile, view) items
+// of all of them through its view buffers, so the per-CTA set-up (barriers, the active-view list,
+// twiddles) is paid once per CTA rather than once per tile; each thread loads its next tile's Green
+// values from the octant right after its last Green multiply of the current tile, and they land
+// while the inverse transform of that view and the forward transform of the next item run.  Which
+// form is faster depends on the views per launch (the autotuner times both).
+template <int L, bool ALT, bool PERSIST>
+__global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const __grid_constant__ ZParams a) {
+  using W = ZW<L, ALT>;
+  static_assert(!PERSIST || W::GREG, "the persistent z pass keeps its Green values in registers");
   constexpr int R1 = W::R1, R2 = W::R2, P = W::P, NZ = W::NZ, CPW = W::CPW, T = W::T, NW = W::NW;
   static_assert(W::ok, "k_zw needs T | 32");
   static_assert(R1 % 2 == 0 && R2 % 2 == 0 && W::XP % 2 == 0, "16-byte exchange reads need even rows");
@@ -336,7 +346,7 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
     mbar_init_fence();
     for (int k = 0; k < NS && k < nitems; ++k) item_load(k, k);
   }
-  if constexpr (!GREG) {
+  if constexpr (!PERSIST) {
     // one tile per CTA (the launch has one CTA per tile): its Green tile, kz folded into [0, NZ]
     const int ky = blockIdx.x / tiles_c, kx0 = (blockIdx.x % tiles_c) * P;
     const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
@@ -390,10 +400,16 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
   // where they fit (R2 <= 16); longer splits read them from the shared tile for every view
   float2 g[GREG ? R2 : 1];
   if constexpr (GREG) {
-    if (stage2_thread) load_green<L, R1, R2>(g, a, blockIdx.x / tiles_c, (blockIdx.x % tiles_c) * P + c, t);
-    else
+    if (PERSIST && stage2_thread) {
+      load_green<L, R1, R2>(g, a, blockIdx.x / tiles_c, (blockIdx.x % tiles_c) * P + c, t);
+    } else {
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) g[k2] = make_float2(0.f, 0.f);
+      for (int k2 = 0; k2 < R2; ++k2)
+        g[k2] = stage2_thread ? (k2 < R2 / 2 ? gc[(t + R1 * k2) * W::GR] : gc[(L - R1 * k2 - t) * W::GR])
+                              : make_float2(0.f, 0.f);
+      // the exchange area overlays the Green tile: every compute warp has its values before any writes
+      if constexpr (!PERSIST) asm volatile("bar.sync 1, %0;\n" ::"r"(NW * 32) : "memory");
+    }
   }
 #pragma unroll 1
   for (int i = 0; i < nitems; ++i) {
@@ -445,7 +461,7 @@ __global__ void __launch_bounds__(ZW<L>::NT, ZW<L>::MINB) k_zw(const __grid_cons
         }
         // last view of this tile: the next tile's Green values, in flight during the rest of this
         // view and the forward transform of the next item
-        if (iv == nact - 1 && i + 1 < nitems) {
+        if (PERSIST && iv == nact - 1 && i + 1 < nitems) {
           const int j = (int)blockIdx.x + (i / nact + 1) * (int)gridDim.x;
           load_green<L, R1, R2>(g, a, j / tiles_c, (j % tiles_c) * P + c, t);
         }
@@ -527,9 +543,14 @@ struct ZG {
   static constexpr int TWA = R1 + 2, TWB = R2 + 2;
   static constexpr size_t r16(size_t b) { return (b + 15) / 16 * 16; }
   static constexpr size_t stage_bytes = (size_t)NZ * P * sizeof(float2);
+  // Green rows [kz][P + 8] of the non-persistent form: the two rows of a half-warp's reads are 8
+  // words apart; the exchange area overlays the Green tile
+  static constexpr int GR = P + 8;
+  static constexpr size_t g_bytes = r16((size_t)(NZ + 1) * GR * sizeof(float2));
   static constexpr size_t x_bytes = r16((size_t)P * XP * sizeof(float2));
-  static constexpr size_t off_x = NS * stage_bytes;   // (the Green values are loaded into registers)
-  static constexpr size_t off_twa = off_x + x_bytes;
+  static constexpr size_t off_x = NS * stage_bytes;
+  static constexpr size_t off_g = off_x;
+  static constexpr size_t off_twa = off_x + (g_bytes > x_bytes ? g_bytes : x_bytes);
   static constexpr size_t off_twb = off_twa + r16((size_t)R2 * TWA * sizeof(float2));
   static constexpr size_t off_bar = off_twb + r16((size_t)R1 * TWB * sizeof(float2));
   static constexpr int NBAR = 2 * NS + 1;                                     // full[NS], done[NS], never
@@ -564,7 +585,7 @@ __device__ __forceinline__ bool group_all(int gi, bool v) {
   return gi == 0 ? named_all<2, N>(v) : named_all<3, N>(v);
 }
 
-template <int L>
+template <int L, bool PERSIST>
 __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_constant__ ZParams a) {
   using W = ZG<L>;
   constexpr int R1 = W::R1, R2 = W::R2, P = W::P, NZ = W::NZ, T = W::T, S1 = W::S1, CG = W::CG, WG = W::WG,
@@ -576,6 +597,7 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
   unsigned char* base = zg_raw + (((raw + 1023u) & ~1023u) - raw);
   float2* stage = reinterpret_cast<float2*>(base);
   float2* xs = reinterpret_cast<float2*>(base + W::off_x);
+  float2* gs = reinterpret_cast<float2*>(base + W::off_g);
   float2* twa = reinterpret_cast<float2*>(base + W::off_twa);
   float2* twb = reinterpret_cast<float2*>(base + W::off_twb);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);   // [NS]: an item's tile has landed
@@ -590,7 +612,7 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
   const int warp = tid >> 5, lane = tid & 31;
   const int tiles_c = 2 * a.nx / P;
   const int ntiles = tiles_c * 2 * a.ny;
-  // persistent, as k_zw: tiles blockIdx.x + k gridDim.x, items i = k nact + view
+  // as k_zw: one tile per CTA, or persistent (tiles blockIdx.x + k gridDim.x), items i = k nact + view
   const int ntl = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int nitems = ntl * nact;
   const bool producer = warp == NW;
@@ -610,6 +632,16 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
     mbar_init(never, 1);
     mbar_init_fence();
     for (int k = 0; k < NS && k < nitems; ++k) item_load(k, k);
+  }
+  if constexpr (!PERSIST) {
+    // the CTA's one tile: its Green tile, kz folded into [0, NZ]
+    const int ky = blockIdx.x / tiles_c, kx0 = (blockIdx.x % tiles_c) * P;
+    const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
+    for (int i = tid; i < (NZ + 1) * P; i += W::NT) {
+      const int kz = i / P, c2 = i % P, kx = kx0 + c2;
+      const int fx = kx <= a.nx ? kx : 2 * a.nx - kx;
+      gs[kz * W::GR + c2] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+    }
   }
   for (int i = tid; i < R1 * R2; i += W::NT) {
     twa[(i / R1) * W::TWA + i % R1] = __ldg(a.zwa + i);
@@ -649,7 +681,15 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
   float2* xc = xs + cc * W::XP;
   // this thread's Green values (kz = t + R1 k2) for the current tile, in registers
   float2 gr[R2];
-  load_green<L, R1, R2>(gr, a, blockIdx.x / tiles_c, (blockIdx.x % tiles_c) * P + cc, t);
+  if constexpr (PERSIST) {
+    load_green<L, R1, R2>(gr, a, blockIdx.x / tiles_c, (blockIdx.x % tiles_c) * P + cc, t);
+  } else {
+    const float2* gc = gs + cc;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) gr[k2] = k2 < R2 / 2 ? gc[(t + R1 * k2) * W::GR] : gc[(L - R1 * k2 - t) * W::GR];
+    // the exchange area overlays the Green tile: every compute warp has its values before any writes
+    named_sync<1, NW * 32>();
+  }
 #pragma unroll 1
   for (int i = 0; i < nitems; ++i) {
     const int buf = i % NS;
@@ -697,7 +737,7 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmul(u[k2], gr[k2]);
     }
-    if (iv == nact - 1 && i + 1 < nitems) {
+    if (PERSIST && iv == nact - 1 && i + 1 < nitems) {
       // last view of this tile: the next tile's Green values, in flight while the transforms run
       const int j = (int)blockIdx.x + (i / nact + 1) * (int)gridDim.x;
       load_green<L, R1, R2>(gr, a, j / tiles_c, (j % tiles_c) * P + cc, t);

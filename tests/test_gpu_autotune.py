@@ -38,6 +38,8 @@ def test_autotune_picks_valid_variants_and_keeps_the_results(monkeypatch):
     assert t["from_cache"] == 0
     assert t["z_tma"] in (0, 1) and t["ix_prefetch"] in (0, 1) and t["fx_views_fastest"] in (0, 1)
     assert t["check_every"] in (2, 4, 8) and t["use_graphs"] in (0, 1)
+    assert t["z_split"] in (0, 1) and t["strided_wide"] in (0, 1) and t["views_per_launch"] in (0, 1, 2, 8)
+    assert t["z_persist"] in (0, 1)
     assert t["matvec_us_per_view"] > 0 and t["solve_ms"] > 0
     u, far, code, stats = plan.forward(f, plan.plane_waves(k))
     torch.cuda.synchronize()
@@ -49,20 +51,29 @@ def test_autotune_picks_valid_variants_and_keeps_the_results(monkeypatch):
     ref.close()
 
 
+# (z_tma, ix_prefetch, fx_views_fastest, check_every, use_graphs, z_split, strided_wide, views_per_launch,
+#  z_persist)
+VARIANTS = [(0, 0, 0, 2, 0, 0, 0, 0, 0), (1, 0, 1, 8, 1, 1, 1, 2, 0), (0, 1, 0, 4, 1, 0, 1, 1, 0),
+            (1, 1, 0, 2, 1, 1, 0, 0, 1), (1, 1, 1, 2, 0, 0, 1, 1, 1), (1, 0, 0, 4, 1, 0, 0, 2, 1)]
+NAMES = ("z_tma", "ix_prefetch", "fx_views_fastest", "check_every", "use_graphs", "z_split", "strided_wide",
+         "views_per_launch", "z_persist")
+
+
 @pytest.mark.gpu
-@pytest.mark.parametrize("variant", [(0, 0, 0, 2, 0), (1, 0, 1, 8, 1), (0, 1, 0, 4, 1)])
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_every_variant_matches_the_oracle(tmp_path, monkeypatch, variant):
     # a cache entry forces the variant without timing anything
     torch, ls = torch_and_lib()
     n = 3
     cache = tmp_path / "tune.txt"
-    cache.write_text(_key(torch, n) + " " + " ".join(str(v) for v in variant) + " 1.0 1.0\n")
+    v = [str(x) for x in variant]
+    cache.write_text(_key(torch, n) + " " + " ".join(v[:5]) + " 1.0 1.0 " + " ".join(v[5:]) + "\n")
     monkeypatch.setenv("LS_AUTOTUNE_CACHE", str(cache))
     f64, f, k = _setup(torch, ls, n)
     plan = ls.Plan(SHAPE, KB, H, tol=1e-6)
     t = plan.autotune(n, f)
     assert t["from_cache"] == 1
-    assert (t["z_tma"], t["ix_prefetch"], t["fx_views_fastest"], t["check_every"], t["use_graphs"]) == variant
+    assert tuple(t[k] for k in NAMES) == variant
     u, far, code, stats = plan.forward(f, plan.plane_waves(k))
     torch.cuda.synchronize()
     assert code == ls.LS_OK, stats
@@ -84,7 +95,7 @@ def test_cache_round_trip(tmp_path, monkeypatch):
     assert cache.read_text().split()[0] == _key(torch, 2)
     second = plan.autotune(2, f)
     assert second["from_cache"] == 1
-    for name in ("z_tma", "ix_prefetch", "fx_views_fastest", "check_every", "use_graphs"):
+    for name in NAMES:
         assert second[name] == first[name]
     assert np.isclose(second["solve_ms"], first["solve_ms"], rtol=1e-3)
     plan.close()

@@ -13,9 +13,9 @@ static int failures = 0;
     }                                                                  \
   } while (0)
 
-template <int L>
+template <int L, bool ALT = false>
 void check() {
-  using W = ZW<L>;
+  using W = ZW<L, ALT>;
   if (!W::ok) return;
   // static shared memory of the kernel: the active-view list, the warp sums and the abort flag
   constexpr size_t static_smem = kMaxLaunchSlots * sizeof(int) + 32 * sizeof(int) + 16;
@@ -56,7 +56,8 @@ void check_groups() {
   REQUIRE(W::stage_bytes % 1024 == 0, L);
   REQUIRE(W::off_x % 16 == 0 && W::off_twa % 16 == 0 && W::off_twb % 16 == 0 && W::off_bar % 16 == 0, L);
   REQUIRE(W::off_x >= (size_t)W::NS * W::stage_bytes, L);
-  REQUIRE(W::off_twa >= W::off_x + W::x_bytes, L);
+  REQUIRE(W::off_twa >= W::off_x + W::x_bytes && W::off_g == W::off_x && W::off_twa >= W::off_g + W::g_bytes, L);
+  REQUIRE(W::GR % 16 == 8 && W::GR >= W::P, L);
   REQUIRE(W::off_twb >= W::off_twa + (size_t)W::R2 * W::TWA * sizeof(float2), L);
   REQUIRE(W::off_bar >= W::off_twb + (size_t)W::R1 * W::TWB * sizeof(float2), L);
   REQUIRE(W::NBAR == 2 * W::NS + 1 && W::smem >= W::off_bar + W::NBAR * sizeof(uint64_t) + 1023, L);
@@ -75,6 +76,9 @@ int main() {
   check_groups<144>(); check_groups<288>();
   check<16>(); check<24>(); check<32>(); check<48>(); check<64>(); check<96>(); check<128>();
   check<144>(); check<192>(); check<256>(); check<288>(); check<384>();
+  // the second splits the autotuner can choose
+  check<16, true>(); check<24, true>(); check<32, true>(); check<48, true>(); check<64, true>(); check<96, true>();
+  check<128, true>(); check<192, true>(); check<256, true>(); check<384, true>();
   printf(failures ? "FAIL\n" : "OK\n");
   return failures ? 1 : 0;
 }
