@@ -410,7 +410,7 @@ def run_gpu(args):
             "mean_adjoint_iterations": float(np.mean(stats_acc["adj_iters"])),
             "worst_status": int(max(stats_acc["status"])),
             "parallelism": f"replicas{ws}" if ws > 1 else "single",
-            "autotune": ({k: tune[k] for k in ("z_tma", "z_split", "z_persist", "strided_wide", "ix_prefetch", "fx_views_fastest",
+            "autotune": ({k: tune[k] for k in ("z_tma", "z_split", "z_persist", "strided_wide", "ix_prefetch", "fx_views_fastest", "fx_bulk",
                                                "views_per_launch", "check_every", "use_graphs", "from_cache")}
                          if tune else "off (defaults)"),
         },
@@ -711,7 +711,7 @@ def run_fista_mode(args):
     gamma0 = 0.5 * float(f_true.abs().max()) / float(d0.abs().max())
     out = {"mode": "fista", "workload": "128^3, 60 views NA 0.8, 20 ellipsoids dn <= 0.1, 1% noise, TV + positivity",
            "iterations": args.fista_iters, "gamma0": gamma0, "tau": args.tau,
-           "autotune": {k: tune[k] for k in ("z_tma", "z_split", "z_persist", "strided_wide", "ix_prefetch", "fx_views_fastest",
+           "autotune": {k: tune[k] for k in ("z_tma", "z_split", "z_persist", "strided_wide", "ix_prefetch", "fx_views_fastest", "fx_bulk",
                                              "views_per_launch", "check_every", "use_graphs")}}
     for name, batched, warm in (("batched", True, False), ("batched_warm_start", True, True),
                                 ("one_view_at_a_time", False, False)):
@@ -796,7 +796,7 @@ def run_bead_mode(args):
                 "z_pass_gbs": round(z_gbs, 1) if z_gbs else None,
                 "z_kernel": ("k_zg (TMA-staged column groups)" if tune["z_tma"] else "k_z (cp.async staging)")
                 if 2 * n in (144, 288) else ("k_zw" if tune["z_tma"] else "k_z (cp.async staging)"),
-                "autotune": {k: tune[k] for k in ("z_tma", "z_split", "z_persist", "strided_wide", "ix_prefetch", "fx_views_fastest",
+                "autotune": {k: tune[k] for k in ("z_tma", "z_split", "z_persist", "strided_wide", "ix_prefetch", "fx_views_fastest", "fx_bulk",
                                                   "views_per_launch", "check_every", "use_graphs")},
             }
         plan.close()

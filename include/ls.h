@@ -105,6 +105,7 @@ typedef struct {
   int strided_wide;           /* 1: the y passes with 32 pencils per CTA (else 16)                             */
   int views_per_launch;       /* BiCGStab iteration launched over chunks of this many views (0: all at once)   */
   int z_persist;              /* 1: the TMA-staged z pass persistent (one wave of CTAs streaming their tiles)  */
+  int fx_bulk;                /* 1: the first pass with bulk-copy-staged input rows (persistent)              */
 } ls_tune;
 
 /* Fill *opt with the defaults listed above. */

@@ -75,7 +75,7 @@ class ls_tune(C.Structure):
     _fields_ = [("z_tma", C.c_int), ("ix_prefetch", C.c_int), ("fx_views_fastest", C.c_int),
                 ("check_every", C.c_int), ("use_graphs", C.c_int), ("matvec_us_per_view", C.c_double),
                 ("solve_ms", C.c_double), ("from_cache", C.c_int), ("z_split", C.c_int), ("strided_wide", C.c_int),
-                ("views_per_launch", C.c_int), ("z_persist", C.c_int)]
+                ("views_per_launch", C.c_int), ("z_persist", C.c_int), ("fx_bulk", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

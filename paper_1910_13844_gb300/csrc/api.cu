@@ -267,6 +267,9 @@ static FxParams fx_base(ls_plan* P, SlotSel sel, int rows) {
   a.dst_stride = P->eng.a1_stride;
   a.tw2 = P->tw2_x;
   a.views_fastest = P->tune_fx_views_fastest;
+  a.bulk = P->tune_fx_bulk;
+  a.sms = P->sms;
+  a.err = P->eng.counts_d + 4;
   return a;
 }
 
@@ -524,7 +527,8 @@ int ensure_iter_graph(ls_plan* P, int nslots) {
   // the captured launches carry the plan's launch variants: recapture when ls_autotune changed them
   const int variant = P->tune_z_tma | P->tune_ix_prefetch << 1 | P->tune_fx_views_fastest << 2 |
                       (P->inj_z_stall || P->inj_z_wait_ns ? 1 << 3 : 0) | P->tune_z_split << 4 |
-                      P->tune_strided_wide << 5 | P->tune_z_persist << 6 | P->tune_views_per_launch << 7;
+                      P->tune_strided_wide << 5 | P->tune_z_persist << 6 | P->tune_fx_bulk << 7 |
+                      P->tune_views_per_launch << 8;
   if (e.iter_graph && e.iter_graph_slots == nslots && e.iter_graph_variant == variant) return LS_OK;
   if (e.iter_graph) {
     cudaGraphExecDestroy(e.iter_graph);
@@ -551,6 +555,7 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   v.twa_z = P->twa_z; v.twb_z = P->twb_z; v.zwa_z = P->zwa_z; v.zwb_z = P->zwb_z;
   v.zwa2_z = P->zwa2_z; v.zwb2_z = P->zwb2_z;
   v.tune_z_split = P->tune_z_split; v.tune_strided_wide = P->tune_strided_wide; v.tune_z_persist = P->tune_z_persist;
+  v.tune_fx_bulk = P->tune_fx_bulk;
   v.tune_views_per_launch = P->tune_views_per_launch;
   v.gocta = P->gocta; v.k2hat = P->k2hat; v.p_built = P->p_built;
   v.device = P->device; v.sms = P->sms;
@@ -586,6 +591,7 @@ ls_plan* plan_clone_shared(const ls_plan* P) {
   c->twa_z = P->twa_z; c->twb_z = P->twb_z; c->zwa_z = P->zwa_z; c->zwb_z = P->zwb_z;
   c->zwa2_z = P->zwa2_z; c->zwb2_z = P->zwb2_z;
   c->tune_z_split = P->tune_z_split; c->tune_strided_wide = P->tune_strided_wide; c->tune_z_persist = P->tune_z_persist;
+  c->tune_fx_bulk = P->tune_fx_bulk;
   c->tune_views_per_launch = P->tune_views_per_launch;
   c->gocta = P->gocta; c->k2hat = P->k2hat; c->p_built = P->p_built;
   c->device = P->device; c->sms = P->sms;
@@ -644,7 +650,7 @@ int engine_solve(ls_plan* P, int nslots, cudaStream_t st) {
     LS_CUDA_TRY(cudaStreamSynchronize(st));
     prof_resolve(P, false);
     if (e.counts_h[4]) {
-      set_last_error("a TMA copy of the z pass did not complete within its time limit");
+      set_last_error("a TMA copy of the z pass or a bulk copy of the first pass did not complete within its time limit");
       return LS_ECUDA;
     }
     const int n_iter = e.counts_h[0], n_resid = e.counts_h[1];

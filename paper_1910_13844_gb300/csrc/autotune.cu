@@ -8,6 +8,8 @@
 //   * FY / IY: 16 or 32 pencils per CTA;
 //   * IX: L2 prefetch of its epilogue operands at kernel start, or not;
 //   * FX: launch grid with the views fastest (shared potential rows from L2), or the rows fastest;
+//     or the bulk-copy-staged persistent kernel (input rows staged in shared memory, three row blocks
+//     ahead);
 //   * the solve loop: the views per launch of an iteration (all, or chunks of n/2, n/4 or 8 views,
 //     each chunk one launch per pass), iterations between host reads of the convergence mask
 //     (2, 4, 8), and replay of the iteration from a captured CUDA graph or direct launches.
@@ -53,9 +55,9 @@ static bool cache_lookup(const std::string& key, ls_tune* t) {
   bool found = false;
   char line[512];
   while (fgets(line, sizeof(line), fp)) {
-    if (sscanf(line, "%255s %d %d %d %d %d %lf %lf %d %d %d %d", k, &v.z_tma, &v.ix_prefetch, &v.fx_views_fastest,
-               &v.check_every, &v.use_graphs, &v.matvec_us_per_view, &v.solve_ms, &v.z_split, &v.strided_wide,
-               &v.views_per_launch, &v.z_persist) == 12 &&
+    if (sscanf(line, "%255s %d %d %d %d %d %lf %lf %d %d %d %d %d", k, &v.z_tma, &v.ix_prefetch,
+               &v.fx_views_fastest, &v.check_every, &v.use_graphs, &v.matvec_us_per_view, &v.solve_ms, &v.z_split,
+               &v.strided_wide, &v.views_per_launch, &v.z_persist, &v.fx_bulk) == 13 &&
         key == k) {
       *t = v;   // the last entry for a key wins
       found = true;
@@ -71,9 +73,9 @@ static void cache_store(const std::string& key, const ls_tune& t) {
   std::lock_guard<std::mutex> lock(g_cache_mu);
   FILE* fp = fopen(path, "a");
   if (!fp) return;
-  fprintf(fp, "%s %d %d %d %d %d %.9g %.9g %d %d %d %d\n", key.c_str(), t.z_tma, t.ix_prefetch, t.fx_views_fastest,
-          t.check_every, t.use_graphs, t.matvec_us_per_view, t.solve_ms, t.z_split, t.strided_wide, t.views_per_launch,
-          t.z_persist);
+  fprintf(fp, "%s %d %d %d %d %d %.9g %.9g %d %d %d %d %d\n", key.c_str(), t.z_tma, t.ix_prefetch,
+          t.fx_views_fastest, t.check_every, t.use_graphs, t.matvec_us_per_view, t.solve_ms, t.z_split, t.strided_wide,
+          t.views_per_launch, t.z_persist, t.fx_bulk);
   fclose(fp);
 }
 
@@ -87,6 +89,7 @@ static void apply(ls_plan* P, const ls_tune& t) {
   P->tune_strided_wide = t.strided_wide;
   P->tune_views_per_launch = t.views_per_launch;
   P->tune_z_persist = t.z_persist;
+  P->tune_fx_bulk = t.fx_bulk;
 }
 
 // mean milliseconds of `reps` calls of fn after one untimed call; negative on error
@@ -160,6 +163,7 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   cur.strided_wide = 0;
   cur.views_per_launch = 0;
   cur.z_persist = 0;
+  cur.fx_bulk = 0;
   cur.from_cache = 0;
   auto matvec = [&] { return tune_matvec(P, f, n_views, st); };
   auto tune_op = [&](int* knob, int n_values, const int* values) -> double {
@@ -183,6 +187,7 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   mv_ms = tune_op(&cur.strided_wide, 2, two);
   mv_ms = tune_op(&cur.ix_prefetch, 2, two);
   mv_ms = tune_op(&cur.fx_views_fastest, 2, two);
+  mv_ms = tune_op(&cur.fx_bulk, 2, two);
   // solve loop: forward solves of the plane waves
   auto solve = [&] { return tune_forward(P, f, n_views, st); };
   auto solve_views = solve;

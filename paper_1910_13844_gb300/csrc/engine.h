@@ -79,6 +79,7 @@ struct ls_plan {
   int tune_fx_views_fastest = 0;  // FX grid with views fastest (else row blocks fastest)
   int tune_z_split = 0;           // TMA-staged z pass with its second radix split
   int tune_z_persist = 0;         // persistent TMA-staged z pass
+  int tune_fx_bulk = 0;           // bulk-copy-staged persistent first pass
   int tune_strided_wide = 0;      // FY/IY with 32 pencils per CTA (else 16)
   int tune_views_per_launch = 0;  // BiCGStab iteration launched over chunks of this many views (0: all)
   // test-only failure injection (ls_debug_inject); the defaults inject nothing

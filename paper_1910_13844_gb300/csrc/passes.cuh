@@ -138,6 +138,164 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 6) k_fx(FxParams a) {
   }
 }
 
+// ------------------------------------------------------------------------- FX (bulk-copy staged)
+// The same pass with the rows of every input vector staged in shared memory by bulk copies
+// (cp.async.bulk, one per vector and row block: the rows of a block are contiguous), NSTG row blocks
+// ahead, behind one mbarrier per stage.  Persistent: one CTA per SM walks the (active view, row
+// block) items blockIdx.x, blockIdx.x + gridDim.x, ...; a thread loads its inputs from shared memory
+// instead of issuing eight 8-byte loads per vector.  A potential row that is not 16-byte aligned is
+// read from global memory instead of staged.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+template <int L>
+struct FXB {
+  using G = Geo<L>;
+  static constexpr int PC = G::PC, NX = L / 2;
+  static constexpr int NSTG = 3;                                        // row blocks in flight per CTA
+  static constexpr size_t vec_bytes = (size_t)PC * NX * sizeof(float2);
+  static constexpr size_t f_bytes = (size_t)PC * NX * sizeof(float);
+  static constexpr size_t stage_bytes = 3 * vec_bytes + f_bytes;       // r, v, p and f (the BiCGStab p update)
+  static constexpr size_t off_x = NSTG * stage_bytes;                  // exchange area of the two DFT stages
+  static constexpr size_t off_bar = off_x + (G::smem_contig + 15) / 16 * 16;
+  static constexpr size_t smem = off_bar + NSTG * sizeof(uint64_t);
+  static constexpr bool ok = smem <= 227 * 1024 && stage_bytes % 16 == 0 && vec_bytes % 16 == 0;
+};
+
+template <int L>
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 1) k_fxb(FxParams a) {
+  using G = Geo<L>;
+  using B = FXB<L>;
+  constexpr int R1 = G::R1, R2 = G::R2, PC = G::PC, NX = B::NX, NSTG = B::NSTG;
+  constexpr int NT = G::T * G::PC;
+  extern __shared__ __align__(16) unsigned char fxb_raw[];
+  float2* S0 = reinterpret_cast<float2*>(fxb_raw + B::off_x);
+  uint64_t* full = reinterpret_cast<uint64_t*>(fxb_raw + B::off_bar);
+  __shared__ int s_list[kMaxLaunchSlots];
+  __shared__ int s_ws[32];
+  __shared__ int s_fb[NSTG];   // stage s holds the potential's rows
+  const int nact = build_active(a.sel, s_list, s_ws);
+  if (nact == 0) return;
+  const int t = threadIdx.x, p = threadIdx.y, tid = p * G::T + t;
+  const int nrb = (a.rows + PC - 1) / PC;
+  const int nitems = nact * nrb;
+  const int nmine = (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  if (nmine <= 0) return;
+  const int nvec = a.mode == FX_BICG_P ? 3 : a.mode == FX_BICG_S ? 2 : 1;   // src (r), v, p
+  auto stage = [&](int s) { return fxb_raw + (size_t)s * B::stage_bytes; };
+  // issue the copies of this CTA's m-th item into stage s (thread 0)
+  auto issue = [&](int m, int s) {
+    const int k = (int)blockIdx.x + m * (int)gridDim.x;
+    const int slot = active_slot(s_list[k / nrb]);
+    const int row0 = (k % nrb) * PC;
+    const int nrows = min(PC, a.rows - row0);
+    const unsigned vb = (unsigned)(nrows * NX * sizeof(float2));
+    const size_t voff = (size_t)slot * a.vstride + (size_t)row0 * NX;
+    const float* f = a.mode == FX_COPY ? nullptr : slot_f(a.sel, slot) + (size_t)row0 * NX;
+    const bool fb = f && ((reinterpret_cast<uintptr_t>(f) & 15) == 0);
+    s_fb[s] = fb ? 1 : 0;
+    mbar_expect_tx(&full[s], (unsigned)(nvec * vb + (fb ? nrows * NX * sizeof(float) : 0)));
+    unsigned char* st = stage(s);
+    bulk_load(st, a.src + voff, vb, &full[s]);
+    if (nvec >= 2) bulk_load(st + B::vec_bytes, a.vv + voff, vb, &full[s]);
+    if (nvec >= 3) bulk_load(st + 2 * B::vec_bytes, a.vp + voff, vb, &full[s]);
+    if (fb) bulk_load(st + 3 * B::vec_bytes, f, (unsigned)(nrows * NX * sizeof(float)), &full[s]);
+  };
+  if (tid == 0) {
+    for (int s = 0; s < NSTG; ++s) mbar_init(&full[s], 1);
+    mbar_init_fence();
+    for (int m = 0; m < NSTG && m < nmine; ++m) issue(m, m);
+  }
+  __syncthreads();
+  for (int m = 0; m < nmine; ++m) {
+    const int s = m % NSTG;
+    const bool ok = mbar_wait(&full[s], (unsigned)(m / NSTG) & 1u);
+    if (!__syncthreads_and(ok)) {
+      // a copy did not land within its time limit: flag the launch, give the copies still in flight
+      // into this CTA's stages a bounded time to land, and stop
+      if (tid == 0) {
+        atomicExch(a.err, 1);
+        for (int q = m; q < m + NSTG && q < nmine; ++q) mbar_wait(&full[q % NSTG], (unsigned)(q / NSTG) & 1u);
+      }
+      __syncthreads();
+      return;
+    }
+    const int k = (int)blockIdx.x + m * (int)gridDim.x;
+    const int slot = active_slot(s_list[k / nrb]);
+    const int rb = k % nrb;
+    count_run_if(a.sel, rb == 0);
+    const int row = rb * PC + p;
+    const bool valid = row < a.rows;
+    const unsigned char* st = stage(s);
+    const float2* r_s = reinterpret_cast<const float2*>(st) + (size_t)p * NX;
+    const float2* v_s = reinterpret_cast<const float2*>(st + B::vec_bytes) + (size_t)p * NX;
+    const float2* p_s = reinterpret_cast<const float2*>(st + 2 * B::vec_bytes) + (size_t)p * NX;
+    const float* f_s = reinterpret_cast<const float*>(st + 3 * B::vec_bytes) + (size_t)p * NX;
+    const bool fb = s_fb[s] != 0;
+    const float* f = slot_f(a.sel, slot);
+    const size_t voff = (size_t)slot * a.vstride + (size_t)row * NX;
+    float2 v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+    if (valid && t < R2) {
+      float fa = 1.f, fbb = 0.f, al_re = 0.f, al_im = 0.f, om_re = 0.f, om_im = 0.f;
+      bool first = false;
+      if (a.mode == FX_BICG_P) {
+        const SlotDev& sd = a.sel.slots[slot];
+        first = sd.first != 0;
+        fa = (float)sd.beta.x; fbb = (float)sd.beta.y;
+        om_re = (float)sd.omega.x; om_im = (float)sd.omega.y;
+      } else if (a.mode == FX_BICG_S) {
+        const SlotDev& sd = a.sel.slots[slot];
+        al_re = (float)sd.alpha.x; al_im = (float)sd.alpha.y;
+      }
+#pragma unroll
+      for (int n1 = 0; n1 < R1 / 2; ++n1) {
+        const int x = R2 * n1 + t;
+        float2 val = r_s[x];
+        if (a.mode == FX_BICG_P) {
+          if (!first) {
+            // p = r + beta (p - omega v)
+            const float2 d = csub(p_s[x], cmul(make_float2(om_re, om_im), v_s[x]));
+            val = cadd(val, cmul(make_float2(fa, fbb), d));
+          }
+          a.vp[voff + x] = val;
+        } else if (a.mode == FX_BICG_S) {
+          // s = r - alpha v
+          val = csub(val, cmul(make_float2(al_re, al_im), v_s[x]));
+          a.vs[voff + x] = val;
+        }
+        if (a.mode != FX_COPY) val = cscale(val, fb ? f_s[x] : __ldg(f + (size_t)row * NX + x));
+        v[n1] = val;
+      }
+    }
+    float2* S = S0 + (size_t)p * R1 * G::SROW;
+    if (t < R2) {
+      Dft<R1, -1, R1 / 2, R1>::run(v);
+#pragma unroll
+      for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], __ldg(a.tw2 + k1 * R2 + t));
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) S[k1 * G::SROW + t] = v[k1];
+    }
+    __syncthreads();
+    // every thread has read its inputs from stage s: refill it with the item NSTG ahead
+    if (tid == 0 && m + NSTG < nmine) issue(m + NSTG, s);
+    if (valid && t < R1) {
+      float2 u[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) u[n2] = S[t * G::SROW + n2];
+      Dft<R2, -1>::run(u);
+      float2* d = a.dst + (size_t)slot * a.dst_stride + (size_t)row * L;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) d[t + R1 * k2] = u[k2];
+    }
+    __syncthreads();   // the exchange area is free for the next item
+  }
+  (void)NT;
+}
+
 // ------------------------------------------------------------------------- FY / IY
 // Pencils along a strided axis; tile = 16 consecutive entries of the contiguous axis.
 // P = 16 or 32 pencils per CTA (P 8-byte entries of a row: 128 or 256 contiguous bytes per load).
@@ -307,7 +465,15 @@ struct PassLaunch {
 template <int L>
 struct PassImpl {
   using G = Geo<L>;
+  static bool aligned16(const void* q) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
   static void fx(const FxParams& a, int nslots, cudaStream_t st) {
+    if constexpr (FXB<L>::ok) {
+      if (a.bulk && a.sms > 0 && a.err && aligned16(a.src) && aligned16(a.vv) && aligned16(a.vp) && a.vstride % 2 == 0) {
+        const int nrb = (a.rows + G::PC - 1) / G::PC;
+        k_fxb<L><<<std::min(nrb * nslots, a.sms), dim3(G::T, G::PC), FXB<L>::smem, st>>>(a);
+        return;
+      }
+    }
     const unsigned rbs = (unsigned)((a.rows + G::PC - 1) / G::PC);
     dim3 blk(G::T, G::PC), grd = a.views_fastest ? dim3(nslots, rbs) : dim3(rbs, nslots);
     k_fx<L><<<grd, blk, G::smem_contig, st>>>(a);
@@ -382,6 +548,8 @@ struct PassImpl {
     cudaError_t e = cudaSuccess;
     {
       e = cudaFuncSetAttribute(k_fx<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
+      if constexpr (FXB<L>::ok)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fxb<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FXB<L>::smem);
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ix<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, -1, G::PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, +1, G::PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);

@@ -329,12 +329,12 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
   const bool producer = warp == NW;
   // per-view wait limit (read from the parameter space where it is used, not held in a register)
 #define LS_ZW_LIMIT (a.wait_ns ? a.wait_ns : 1000000000ull)
-  // TMA coordinates of item i: (2 kx0 floats, ky, 0, slot)
-  auto item_load = [&](int i, int buf) {
-    const int j = (int)blockIdx.x + (i / nact) * (int)gridDim.x;
+  // TMA coordinates of the item (view position iv, tile number kt of this CTA): (2 kx0 floats, ky, 0, slot)
+  auto item_load = [&](int iv, int kt, int buf) {
+    const int j = (int)blockIdx.x + kt * (int)gridDim.x;
     mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
     tma_load_4d(stage + (size_t)buf * NZ * P, &a.tmap, &full[buf], 2 * (j % tiles_c) * P, j / tiles_c, 0,
-                a.slot0 + active_slot(s_list[i % nact]));
+                a.slot0 + active_slot(s_list[iv]));
   };
   if (producer && lane == 0) {
     s_abort = 0;
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
     }
     mbar_init(never, 1);
     mbar_init_fence();
-    for (int k = 0; k < NS && k < nitems; ++k) item_load(k, k);
+    for (int k = 0; k < NS && k < nitems; ++k) item_load(k % nact, k / nact, k);
   }
   if constexpr (!PERSIST) {
     // one tile per CTA (the launch has one CTA per tile): its Green tile, kz folded into [0, NZ]
@@ -365,18 +365,22 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
     // producer: after the compute warps release an item's buffer, store it and refill it with the
     // item NS ahead
     if (lane != 0) return;
+    // (view position, tile number) of the item being stored and of the one NS ahead, kept by counting
+    int sv = 0, skt = 0, lv = NS % nact, lkt = NS / nact;
     int i = 0;
     for (; i < nitems; ++i) {
       const int buf = i % NS;
       if (!mbar_wait_abort(&done[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZW_LIMIT)) break;
-      const int j = (int)blockIdx.x + (i / nact) * (int)gridDim.x;
+      const int j = (int)blockIdx.x + skt * (int)gridDim.x;
       tma_store_4d(&a.tmap, stage + (size_t)buf * NZ * P, 2 * (j % tiles_c) * P, j / tiles_c, 0,
-                   a.slot0 + active_slot(s_list[i % nact]));
+                   a.slot0 + active_slot(s_list[sv]));
       bulk_commit();
       if (i + NS < nitems) {
         bulk_wait_read_all();   // the store has read the buffer
-        item_load(i + NS, buf);
+        item_load(lv, lkt, buf);
       }
+      if (++sv == nact) { sv = 0; ++skt; }
+      if (++lv == nact) { lv = 0; ++lkt; }
     }
     bulk_wait_read_all();
     if (i < nitems) {
@@ -411,10 +415,10 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
       if constexpr (!PERSIST) asm volatile("bar.sync 1, %0;\n" ::"r"(NW * 32) : "memory");
     }
   }
+  int iv = 0, kt = 0;   // view position and tile number of item i, kept by counting
 #pragma unroll 1
   for (int i = 0; i < nitems; ++i) {
     const int buf = i % NS;
-    const int iv = i % nact;
     const bool ok = (a.stall && i == 0) ? mbar_wait_abort(never, 0u, &s_abort, LS_ZW_LIMIT)
                                         : mbar_wait_abort(&full[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZW_LIMIT);
     if (!__all_sync(0xffffffffu, ok)) break;
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
         // last view of this tile: the next tile's Green values, in flight during the rest of this
         // view and the forward transform of the next item
         if (PERSIST && iv == nact - 1 && i + 1 < nitems) {
-          const int j = (int)blockIdx.x + (i / nact + 1) * (int)gridDim.x;
+          const int j = (int)blockIdx.x + (kt + 1) * (int)gridDim.x;
           load_green<L, R1, R2>(g, a, j / tiles_c, (j % tiles_c) * P + c, t);
         }
       } else if (adj) {
@@ -503,6 +507,7 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
     fence_async_smem();
     __syncwarp();
     if (lane == 0) mbar_arrive(&done[buf]);
+    if (++iv == nact) { iv = 0; ++kt; }
   }
 #undef LS_ZW_LIMIT
 }
@@ -617,11 +622,12 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
   const int nitems = ntl * nact;
   const bool producer = warp == NW;
 #define LS_ZG_LIMIT (a.wait_ns ? a.wait_ns : 1000000000ull)
-  auto item_load = [&](int i, int buf) {
-    const int j = (int)blockIdx.x + (i / nact) * (int)gridDim.x;
+  // TMA coordinates of the item (view position iv, tile number kt of this CTA): (2 kx0 floats, ky, 0, slot)
+  auto item_load = [&](int iv, int kt, int buf) {
+    const int j = (int)blockIdx.x + kt * (int)gridDim.x;
     mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
     tma_load_4d(stage + (size_t)buf * NZ * P, &a.tmap, &full[buf], 2 * (j % tiles_c) * P, j / tiles_c, 0,
-                a.slot0 + active_slot(s_list[i % nact]));
+                a.slot0 + active_slot(s_list[iv]));
   };
   if (producer && lane == 0) {
     s_abort = 0;
@@ -631,7 +637,7 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
     }
     mbar_init(never, 1);
     mbar_init_fence();
-    for (int k = 0; k < NS && k < nitems; ++k) item_load(k, k);
+    for (int k = 0; k < NS && k < nitems; ++k) item_load(k % nact, k / nact, k);
   }
   if constexpr (!PERSIST) {
     // the CTA's one tile: its Green tile, kz folded into [0, NZ]
@@ -650,18 +656,22 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
   __syncthreads();
   if (producer) {
     if (lane != 0) return;
+    // (view position, tile number) of the item being stored and of the one NS ahead, kept by counting
+    int sv = 0, skt = 0, lv = NS % nact, lkt = NS / nact;
     int i = 0;
     for (; i < nitems; ++i) {
       const int buf = i % NS;
       if (!mbar_wait_abort(&done[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZG_LIMIT)) break;
-      const int j = (int)blockIdx.x + (i / nact) * (int)gridDim.x;
+      const int j = (int)blockIdx.x + skt * (int)gridDim.x;
       tma_store_4d(&a.tmap, stage + (size_t)buf * NZ * P, 2 * (j % tiles_c) * P, j / tiles_c, 0,
-                   a.slot0 + active_slot(s_list[i % nact]));
+                   a.slot0 + active_slot(s_list[sv]));
       bulk_commit();
       if (i + NS < nitems) {
         bulk_wait_read_all();   // the store has read the buffer
-        item_load(i + NS, buf);
+        item_load(lv, lkt, buf);
       }
+      if (++sv == nact) { sv = 0; ++skt; }
+      if (++lv == nact) { lv = 0; ++lkt; }
     }
     bulk_wait_read_all();
     if (i < nitems) {
@@ -690,10 +700,10 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
     // the exchange area overlays the Green tile: every compute warp has its values before any writes
     named_sync<1, NW * 32>();
   }
+  int iv = 0, kt = 0;   // view position and tile number of item i, kept by counting
 #pragma unroll 1
   for (int i = 0; i < nitems; ++i) {
     const int buf = i % NS;
-    const int iv = i % nact;
     const bool ok = (a.stall && i == 0) ? mbar_wait_abort(never, 0u, &s_abort, LS_ZG_LIMIT)
                                         : mbar_wait_abort(&full[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZG_LIMIT);
     // the group agrees (this is also the barrier that frees the exchange area of the previous item)
@@ -739,7 +749,7 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
     }
     if (PERSIST && iv == nact - 1 && i + 1 < nitems) {
       // last view of this tile: the next tile's Green values, in flight while the transforms run
-      const int j = (int)blockIdx.x + (i / nact + 1) * (int)gridDim.x;
+      const int j = (int)blockIdx.x + (kt + 1) * (int)gridDim.x;
       load_green<L, R1, R2>(gr, a, j / tiles_c, (j % tiles_c) * P + cc, t);
     }
     Dft<R2, +1>::run(u);
@@ -774,6 +784,7 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
     fence_async_smem();
     __syncwarp();
     if (lane == 0) mbar_arrive(&done[buf]);
+    if (++iv == nact) { iv = 0; ++kt; }
   }
 #undef LS_ZG_LIMIT
 }
