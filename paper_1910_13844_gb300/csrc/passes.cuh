@@ -470,7 +470,9 @@ struct PassImpl {
     if constexpr (FXB<L>::ok) {
       if (a.bulk && a.sms > 0 && a.err && aligned16(a.src) && aligned16(a.vv) && aligned16(a.vp) && a.vstride % 2 == 0) {
         const int nrb = (a.rows + G::PC - 1) / G::PC;
-        k_fxb<L><<<std::min(nrb * nslots, a.sms), dim3(G::T, G::PC), FXB<L>::smem, st>>>(a);
+        FxParams b = a;
+        b.sel.nslots = nslots;   // the kernel builds its list of active views from the selector
+        k_fxb<L><<<std::min(nrb * nslots, a.sms), dim3(G::T, G::PC), FXB<L>::smem, st>>>(b);
         return;
       }
     }
