@@ -14,8 +14,9 @@
 //     each chunk one launch per pass), iterations between host reads of the convergence mask
 //     (2, 4, 8), and replay of the iteration from a captured CUDA graph or direct launches.
 // Operator variants are timed on batched operator applications, the loop variants on forward solves
-// of plane-wave illuminations.  One knob is tuned at a time, in the order above, keeping the best
-// value of the earlier ones.  Results can be cached in a text file (LS_AUTOTUNE_CACHE) keyed by the
+// of plane-wave illuminations.  Every operator variant's output is first compared with the default
+// variants' (relative L2 over the batch); a variant that differs by more than 1e-5 is never chosen.
+// One knob is tuned at a time, in the order above, keeping the best value of the earlier ones.  Results can be cached in a text file (LS_AUTOTUNE_CACHE) keyed by the
 // device name, the grid and the number of views.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -166,12 +167,48 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   cur.fx_bulk = 0;
   cur.from_cache = 0;
   auto matvec = [&] { return tune_matvec(P, f, n_views, st); };
+  // reference output of the default variants (y = x - G f x over the batch, kept in the s vectors)
+  apply(P, cur);
+  if (matvec() != LS_OK) {
+    P->prof.on = prof;
+    return LS_ECUDA;
+  }
+  LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_S), e.vptr(V_R), (size_t)n_views * e.N * sizeof(float2),
+                              cudaMemcpyDeviceToDevice, st));
+  // relative L2 difference of the current variant's output from the reference (negative on error)
+  auto deviation = [&]() -> double {
+    if (matvec() != LS_OK) return -1.0;
+    std::vector<void*> tab(3 * (size_t)n_views);
+    for (int q = 0; q < n_views; ++q) {
+      tab[q] = e.vptr(V_R, q);
+      tab[n_views + q] = e.vptr(V_S, q);
+      tab[2 * n_views + q] = e.vptr(V_T, q);
+    }
+    if (engine_upload_ptrs(P, 1, (const void* const*)tab.data(), 3 * n_views, st) != LS_OK) return -1.0;
+    void** t1 = engine_ptr_table(P, 1);
+    const int nb = 64;
+    ResidualParams rp{e.N, (const float2* const*)t1, (const float2* const*)(t1 + n_views),
+                      (float2* const*)(t1 + 2 * n_views), e.partials};
+    launch_residual(rp, nb, n_views, st);
+    std::vector<double> h((size_t)n_views * nb * 4);
+    if (cudaMemcpyAsync(h.data(), e.partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return -1.0;
+    double dd = 0.0, rr = 0.0;
+    for (size_t b = 0; b < (size_t)n_views * nb; ++b) {
+      dd += h[4 * b];
+      rr += h[4 * b + 1];
+    }
+    return rr > 0.0 ? sqrt(dd / rr) : sqrt(dd);
+  };
   auto tune_op = [&](int* knob, int n_values, const int* values) -> double {
     double best_ms = -1.0;
     int best_v = *knob;
     for (int i = 0; i < n_values; ++i) {
       *knob = values[i];
       apply(P, cur);
+      const double dev = deviation();
+      if (!(dev >= 0.0 && dev <= 1e-5)) continue;   // not the same operator: never chosen
       const double ms = time_ms(st, 3, matvec);
       if (ms > 0 && (best_ms < 0 || ms < best_ms)) { best_ms = ms; best_v = values[i]; }
     }
