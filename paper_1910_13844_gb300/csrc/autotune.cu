@@ -8,11 +8,11 @@
 //   * FY / IY: 16 or 32 pencils per CTA;
 //   * IX: L2 prefetch of its epilogue operands at kernel start, or not;
 //   * FX: launch grid with the views fastest (shared potential rows from L2), or the rows fastest;
-//     or the bulk-copy-staged persistent kernel (input rows staged in shared memory, three row blocks
-//     ahead);
-//   * the solve loop: the views per launch of an iteration (all, or chunks of n/2, n/4 or 8 views,
-//     each chunk one launch per pass), iterations between host reads of the convergence mask
-//     (2, 4, 8), and replay of the iteration from a captured CUDA graph or direct launches.
+//   * the solve loop: FX in the BiCGStab iteration as the bulk-copy-staged persistent kernel (input rows
+//     staged in shared memory, three row blocks ahead) or not, the views per launch of an iteration
+//     (all, or chunks of n/2, n/4 or 8 views, each chunk one launch per pass), iterations between
+//     host reads of the convergence mask (2, 4, 8), and replay of the iteration from a captured CUDA
+//     graph or direct launches.
 // Operator variants are timed on batched operator applications, the loop variants on forward solves
 // of plane-wave illuminations.  Every operator variant's output is first compared with the default
 // variants' (relative L2 over the batch); a variant that differs by more than 1e-5 is never chosen.
@@ -175,13 +175,13 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   }
   LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_S), e.vptr(V_R), (size_t)n_views * e.N * sizeof(float2),
                               cudaMemcpyDeviceToDevice, st));
-  // relative L2 difference of the current variant's output from the reference (negative on error)
-  auto deviation = [&]() -> double {
-    if (matvec() != LS_OK) return -1.0;
+  // relative L2 difference of the vectors `got` from the reference vectors `ref` over the batch
+  // (negative on error)
+  auto differ = [&](int got, int ref) -> double {
     std::vector<void*> tab(3 * (size_t)n_views);
     for (int q = 0; q < n_views; ++q) {
-      tab[q] = e.vptr(V_R, q);
-      tab[n_views + q] = e.vptr(V_S, q);
+      tab[q] = e.vptr(got, q);
+      tab[n_views + q] = e.vptr(ref, q);
       tab[2 * n_views + q] = e.vptr(V_T, q);
     }
     if (engine_upload_ptrs(P, 1, (const void* const*)tab.data(), 3 * n_views, st) != LS_OK) return -1.0;
@@ -201,6 +201,8 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
     }
     return rr > 0.0 ? sqrt(dd / rr) : sqrt(dd);
   };
+  // the current variant's operator output against the default variants'
+  auto deviation = [&]() -> double { return matvec() == LS_OK ? differ(V_R, V_S) : -1.0; };
   auto tune_op = [&](int* knob, int n_values, const int* values) -> double {
     double best_ms = -1.0;
     int best_v = *knob;
@@ -224,12 +226,25 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   mv_ms = tune_op(&cur.strided_wide, 2, two);
   mv_ms = tune_op(&cur.ix_prefetch, 2, two);
   mv_ms = tune_op(&cur.fx_views_fastest, 2, two);
-  mv_ms = tune_op(&cur.fx_bulk, 2, two);
   // solve loop: forward solves of the plane waves
   auto solve = [&] { return tune_forward(P, f, n_views, st); };
   auto solve_views = solve;
   double sv_ms = -1.0;
   {
+    // the bulk-staged first pass in the iteration: its solution must equal the plain kernel's
+    // (the same arithmetic in the same order) before its time counts
+    {
+      cur.fx_bulk = 0;
+      apply(P, cur);
+      double best_b_ms = time_ms(st, 1, solve_views);
+      LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_S), e.vptr(V_X), (size_t)n_views * e.N * sizeof(float2),
+                                  cudaMemcpyDeviceToDevice, st));
+      cur.fx_bulk = 1;
+      apply(P, cur);
+      const double ms = time_ms(st, 1, solve_views);
+      const double dev = ms > 0 ? differ(V_X, V_S) : -1.0;
+      cur.fx_bulk = (dev >= 0.0 && dev <= 1e-6 && ms > 0 && (best_b_ms < 0 || ms < best_b_ms)) ? 1 : 0;
+    }
     // views per launch of an iteration: all of them, or chunks of n/2, n/4 or 8 views
     int cands[4] = {0, n_views / 2, n_views / 4, 8};
     int best_c = 0;

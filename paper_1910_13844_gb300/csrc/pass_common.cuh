@@ -37,7 +37,7 @@ struct FxParams {
   size_t dst_stride;
   const float2* tw2;           // tw2[k1*R2 + n2] = exp(-2 pi i n2 k1 / L)
   int views_fastest = 0;       // launch grid (slots, row blocks) instead of (row blocks, slots) (autotuned)
-  int bulk = 0;                // bulk-copy-staged persistent variant (autotuned)
+  int bulk = 0;                // bulk-copy-staged persistent variant in the BiCGStab modes (autotuned)
   int sms = 0;                 // SMs of the device (grid of the bulk-staged variant)
   int* err = nullptr;          // set to 1 if a wait for a bulk copy gave up (bulk-staged variant)
 };

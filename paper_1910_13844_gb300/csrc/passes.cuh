@@ -468,7 +468,10 @@ struct PassImpl {
   static bool aligned16(const void* q) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
   static void fx(const FxParams& a, int nslots, cudaStream_t st) {
     if constexpr (FXB<L>::ok) {
-      if (a.bulk && a.sms > 0 && a.err && aligned16(a.src) && aligned16(a.vv) && aligned16(a.vp) && a.vstride % 2 == 0) {
+      // the BiCGStab modes only (three or two staged vectors per row block; with one, the plain
+      // kernel's six CTAs per SM keep more loads in flight)
+      if (a.bulk && a.mode >= FX_BICG_P && a.sms > 0 && a.err && aligned16(a.src) && aligned16(a.vv) &&
+          aligned16(a.vp) && a.vstride % 2 == 0) {
         const int nrb = (a.rows + G::PC - 1) / G::PC;
         FxParams b = a;
         b.sel.nslots = nslots;   // the kernel builds its list of active views from the selector
