@@ -246,7 +246,8 @@ def run_gpu(args):
     shape, Q = w["shape"], w["views"]
     kb = 2 * np.pi * ph.ETA_B / ph.LAMBDA_UM
     t_plan = time.perf_counter()
-    plan = ls.Plan(shape, kb, ph.VOXEL_UM, tol=TOL)
+    # the plan's built-in illumination is the workload's cone (sin theta = NA / eta_b, phi_q = 2 pi q / Q)
+    plan = ls.Plan(shape, kb, ph.VOXEL_UM, tol=TOL, cone_sin_theta=NA / ph.ETA_B)
     torch.cuda.synchronize()
     t_plan = time.perf_counter() - t_plan
     dn = ph.random_ellipsoids(shape, count=w["count"], rmin=w["rmin"], rmax=w["rmax"], dn_max=w["dn_max"],
@@ -274,8 +275,8 @@ def run_gpu(args):
     stats_acc = {"fwd_iters": [], "adj_iters": [], "status": []}
 
     def step(f_dev, y_dev):
-        ls.ls_plane_waves(plan.handle, kvec, uin)
-        c1, s1 = ls.ls_forward(plan.handle, f_dev, uin, u, far)
+        # incident plane waves generated inside the forward call, straight into the solver's vectors
+        c1, s1 = ls.ls_forward(plan.handle, f_dev, None, u, far, n_views=Q)
         loss = ls.ls_residual(far, y_dev, res)
         c2, s2 = ls.ls_gradient(plan.handle, f_dev, res, grad, u_fwd=u, view_weights=weights)
         stats_acc["fwd_iters"].append(np.mean([s["iterations"] for s in s1]))
