@@ -97,6 +97,8 @@ void slot_defaults(const ls_plan* P, SlotDev& s, const float* f, int adjoint) {
   s.max_restarts = P->opt.max_restarts;
   s.tol = P->opt.tol;
   s.alpha = s.omega = s.rho = make_double2(1.0, 0.0);
+  s.alpha_f = s.omega_f = make_float2(1.f, 0.f);
+  s.beta_f = make_float2(0.f, 0.f);
 }
 
 void engine_release(Engine& e) {

@@ -87,6 +87,9 @@ struct SlotDev {
   int max_restarts;
   double tol;
   double2 rho, alpha, omega, beta;   // BiCGStab scalars (complex, float64)
+  float2 alpha_f, omega_f, beta_f;   // the same rounded to float once per scalar step, for the vector kernels
+                                     // (a float64 -> float32 conversion in every thread costs GB300's slow
+                                     // float64 pipe)
   double bnorm2, rnorm2, true_rnorm2;
   double rhnorm2;      // ||rh||^2 of the shadow residual (fixed from the last (re)start)
 };

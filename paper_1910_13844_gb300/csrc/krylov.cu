@@ -25,8 +25,8 @@ __global__ void __launch_bounds__(256, 4) k_update(UpdParams a) {
   if (!slot_runs(a.sel, slot)) return;
   count_run(a.sel);
   const SlotDev& sd = a.sel.slots[slot];
-  const float2 al = make_float2((float)sd.alpha.x, (float)sd.alpha.y);
-  const float2 om = make_float2((float)sd.omega.x, (float)sd.omega.y);
+  const float2 al = sd.alpha_f;
+  const float2 om = sd.omega_f;
   const size_t base = (size_t)slot * a.vstride;
   const float4* p = reinterpret_cast<const float4*>(a.p + base);
   const float4* s = reinterpret_cast<const float4*>(a.s + base);
@@ -174,6 +174,9 @@ __global__ void __launch_bounds__(256) k_scalar(ScalarParams a) {
       sd.first = 0;
     } break;
   }
+  sd.alpha_f = make_float2((float)sd.alpha.x, (float)sd.alpha.y);
+  sd.omega_f = make_float2((float)sd.omega.x, (float)sd.omega.y);
+  sd.beta_f = make_float2((float)sd.beta.x, (float)sd.beta.y);
 }
 
 // Test-only failure injection: zero the shadow residual of one slot at its initial residual

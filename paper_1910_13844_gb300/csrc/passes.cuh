@@ -86,11 +86,11 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 6) k_fx(FxParams a) {
     if (a.mode == FX_BICG_P) {
       const SlotDev& sd = a.sel.slots[slot];
       first = sd.first != 0;
-      fa = (float)sd.beta.x; fb = (float)sd.beta.y;
-      om_re = (float)sd.omega.x; om_im = (float)sd.omega.y;
+      fa = sd.beta_f.x; fb = sd.beta_f.y;
+      om_re = sd.omega_f.x; om_im = sd.omega_f.y;
     } else if (a.mode == FX_BICG_S) {
       const SlotDev& sd = a.sel.slots[slot];
-      al_re = (float)sd.alpha.x; al_im = (float)sd.alpha.y;
+      al_re = sd.alpha_f.x; al_im = sd.alpha_f.y;
     }
 #pragma unroll
     for (int n1 = 0; n1 < R1 / 2; ++n1) {
@@ -245,11 +245,11 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 1) k_fxb(FxParams a) {
       if (a.mode == FX_BICG_P) {
         const SlotDev& sd = a.sel.slots[slot];
         first = sd.first != 0;
-        fa = (float)sd.beta.x; fbb = (float)sd.beta.y;
-        om_re = (float)sd.omega.x; om_im = (float)sd.omega.y;
+        fa = sd.beta_f.x; fbb = sd.beta_f.y;
+        om_re = sd.omega_f.x; om_im = sd.omega_f.y;
       } else if (a.mode == FX_BICG_S) {
         const SlotDev& sd = a.sel.slots[slot];
-        al_re = (float)sd.alpha.x; al_im = (float)sd.alpha.y;
+        al_re = sd.alpha_f.x; al_im = sd.alpha_f.y;
       }
 #pragma unroll
       for (int n1 = 0; n1 < R1 / 2; ++n1) {
