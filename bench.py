@@ -39,6 +39,9 @@ WORKLOADS = {
     # same grid and phantom as "bench" with 4 and 16 views: the cases the full ncu captures run on
     "profile": dict(shape=(128, 128, 128), views=4, count=20, rmin=4.0, rmax=20.0, dn_max=0.05),
     "profile16": dict(shape=(128, 128, 128), views=16, count=20, rmin=4.0, rmax=20.0, dn_max=0.05),
+    # the 144^3 grid of the Fig. 3 bead at lambda/16 (288-point transforms) with 16 views: the case the
+    # column-group z pass is captured on
+    "profile144": dict(shape=(144, 144, 144), views=16, count=20, rmin=4.0, rmax=20.0, dn_max=0.05),
 }
 TOL = 1e-6
 NA = 0.8

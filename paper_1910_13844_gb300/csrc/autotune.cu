@@ -33,6 +33,10 @@ namespace lsgpu {
 
 static std::mutex g_cache_mu;
 
+// forward solves timed per loop variant (after one untimed solve): single solves differ by about 1%,
+// as much as the loop variants themselves
+constexpr int kSolveReps = 3;
+
 static std::string tune_key(const ls_plan* P, int n_views) {
   cudaDeviceProp prop;
   int dev = 0;
@@ -236,12 +240,12 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
     {
       cur.fx_bulk = 0;
       apply(P, cur);
-      double best_b_ms = time_ms(st, 1, solve_views);
+      double best_b_ms = time_ms(st, kSolveReps, solve_views);
       LS_CUDA_TRY(cudaMemcpyAsync(e.vptr(V_S), e.vptr(V_X), (size_t)n_views * e.N * sizeof(float2),
                                   cudaMemcpyDeviceToDevice, st));
       cur.fx_bulk = 1;
       apply(P, cur);
-      const double ms = time_ms(st, 1, solve_views);
+      const double ms = time_ms(st, kSolveReps, solve_views);
       const double dev = ms > 0 ? differ(V_X, V_S) : -1.0;
       cur.fx_bulk = (dev >= 0.0 && dev <= 1e-6 && ms > 0 && (best_b_ms < 0 || ms < best_b_ms)) ? 1 : 0;
     }
@@ -257,7 +261,7 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
       if (seen) continue;
       cur.views_per_launch = cv;
       apply(P, cur);
-      const double ms = time_ms(st, 1, solve_views);
+      const double ms = time_ms(st, kSolveReps, solve_views);
       if (ms > 0 && (best_c_ms < 0 || ms < best_c_ms)) { best_c_ms = ms; best_c = cv; }
     }
     cur.views_per_launch = best_c;
@@ -266,7 +270,7 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
     for (int c : chunks) {
       cur.check_every = c;
       apply(P, cur);
-      const double ms = time_ms(st, 1, solve);
+      const double ms = time_ms(st, kSolveReps, solve);
       if (ms > 0 && (sv_ms < 0 || ms < sv_ms)) { sv_ms = ms; best_v = c; }
     }
     cur.check_every = best_v;
@@ -275,7 +279,7 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
     for (int g : two) {
       cur.use_graphs = g;
       apply(P, cur);
-      const double ms = time_ms(st, 1, solve);
+      const double ms = time_ms(st, kSolveReps, solve);
       if (ms > 0 && (best_g_ms < 0 || ms < best_g_ms)) { best_g_ms = ms; best_g = g; }
     }
     cur.use_graphs = best_g;
