@@ -360,12 +360,25 @@ enum ls_inject_kind {
                               /*   still running report LS_TIMEOUT; value < 0 restores the normal bound     */
   LS_INJECT_ALLOC_FAIL = 3,   /* process-wide (plan may be NULL): the next `value` solver-workspace         */
                               /*   allocations (plans and server lanes) fail with LS_ENOMEM                  */
-  LS_INJECT_Z_STALL = 4       /* plan: value > 0: the TMA-staged z pass waits on a barrier that nothing     */
+  LS_INJECT_Z_STALL = 4,      /* plan: value > 0: the TMA-staged z pass waits on a barrier that nothing     */
                               /*   completes and gives up after `value` ns (every copy it issued is still    */
                               /*   waited for, with the normal one-second bound); the solve returns          */
                               /*   LS_ECUDA.  value = 0 turns it off                                         */
+  LS_INJECT_BOUNDS_PROBE = 5  /* plan: value != 0: in the debug build (ls_debug_bounds) the plain first     */
+                              /*   pass's slot check excludes the launch's last view, which then fails the   */
+                              /*   check (site 0x601) and is skipped; the normal build ignores it           */
 };
 int ls_debug_inject(ls_plan* plan, int kind, long long value);
+
+/* Index checks of the debug build (the paper has no counterpart).  libls_debug.so is the library
+ * compiled with LS_DEBUG_BOUNDS: its hot kernels (the five FFT passes, the bulk-staged first pass,
+ * the z passes and the BiCGStab update) test every checked global or shared-memory index against
+ * the extents of its array; a failing check records a site code (kernel << 8 | access) and the
+ * access is skipped, so a wrong index never faults.  *site (host, may be NULL) receives the first
+ * recorded code over the library's translation units (0: none); clear = 1 resets the records.
+ * Returns 1 in the debug build, 0 in the normal one (*site = 0; nothing is checked), LS_ECUDA if
+ * a record cannot be read.  Reads device memory: call it after the checked work has completed. */
+int ls_debug_bounds(unsigned* site, int clear);
 
 /* Measured FP32 throughput of the current device, for the FP32-pipe roofline of the FFT passes (no
  * counterpart in the paper): out[0] scalar FFMA, out[1] scalar FMUL, out[2] packed add.f32x2, each in

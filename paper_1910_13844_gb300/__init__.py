@@ -17,7 +17,7 @@ import torch
 
 from . import _abi
 from ._abi import (LS_BREAKDOWN, LS_EAGAIN, LS_ECUDA, LS_EINVAL, LS_ENOMEM, LS_ENOTFOUND, LS_EUNSUPPORTED,
-                   LS_INJECT_ALLOC_FAIL, LS_INJECT_MAX_ROUNDS, LS_INJECT_NONE, LS_INJECT_Z_STALL,
+                   LS_INJECT_ALLOC_FAIL, LS_INJECT_BOUNDS_PROBE, LS_INJECT_MAX_ROUNDS, LS_INJECT_NONE, LS_INJECT_Z_STALL,
                    LS_INJECT_ZERO_SHADOW, LS_NOT_CONVERGED, LS_OK, LS_PENDING, LS_REQ_FORWARD, LS_REQ_GRADIENT,
                    LS_TIMEOUT, ls_grid, ls_options, ls_request, ls_result, ls_server_options, ls_stats)
 
@@ -30,7 +30,7 @@ __all__ = [
     "ls_server_destroy", "ls_status_string", "ls_last_error", "ls_workspace_bytes", "ls_profile", "library_path",
     "ls_matvec_noalloc", "ls_matvec_batch", "Server", "ls_set_pupil", "ls_apply_pupil", "ls_incident_field",
     "ls_forward_warm", "ls_prox_tv", "ls_prox_hs", "ls_autotune", "ls_inner_products", "ls_debug_inject",
-    "ls_fp32_peak",
+    "ls_fp32_peak", "ls_debug_bounds",
 ]
 
 _SOFT = (LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN, LS_TIMEOUT, LS_PENDING)
@@ -287,6 +287,16 @@ def ls_fp32_peak(stream=None) -> dict:
     out = (C.c_double * 3)()
     _check(_lib.ls_fp32_peak(out, _stream(stream)), "ls_fp32_peak")
     return {"ffma": out[0], "fmul": out[1], "fadd2": out[2]}
+
+
+def ls_debug_bounds(clear: bool = False):
+    """(checked, site): checked is True in the index-checking build (LS_DEBUG_BOUNDS=1); site is the
+    first failed check's code (0: none)."""
+    site = C.c_uint(0)
+    rc = _lib.ls_debug_bounds(C.byref(site), int(bool(clear)))
+    if rc < 0 or rc > 1:
+        _check(rc, "ls_debug_bounds")
+    return bool(rc), int(site.value)
 
 
 def ls_debug_inject(plan, kind: int, value: int = 0) -> int:

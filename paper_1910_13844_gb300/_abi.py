@@ -5,7 +5,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libls.so")
+# LS_DEBUG_BOUNDS=1 in the environment selects the index-checking build (libls_debug.so)
+DEBUG_BOUNDS = os.environ.get("LS_DEBUG_BOUNDS", "0") == "1"
+LIB_PATH = os.path.join(HERE, "libls_debug.so" if DEBUG_BOUNDS else "libls.so")
 
 LS_OK = 0
 LS_EINVAL = 1
@@ -24,6 +26,7 @@ LS_INJECT_ZERO_SHADOW = 1
 LS_INJECT_MAX_ROUNDS = 2
 LS_INJECT_ALLOC_FAIL = 3
 LS_INJECT_Z_STALL = 4
+LS_INJECT_BOUNDS_PROBE = 5
 
 LS_REQ_FORWARD = 0
 LS_REQ_GRADIENT = 1
@@ -120,19 +123,21 @@ SIGNATURES = {
     "ls_inner_products": (C.c_int, [C.c_int, C.c_size_t, _PP, _PP, C.POINTER(C.c_double), _P]),
     "ls_debug_inject": (C.c_int, [_P, C.c_int, C.c_longlong]),
     "ls_fp32_peak": (C.c_int, [C.POINTER(C.c_double), _P]),
+    "ls_debug_bounds": (C.c_int, [C.POINTER(C.c_uint), C.c_int]),
 }
 
 _lib = None
 
 
 def load() -> C.CDLL:
-    """Load ``libls.so``; raises ImportError when the CUDA library has not been built."""
+    """Load ``libls.so`` (``libls_debug.so`` with LS_DEBUG_BOUNDS=1); raises ImportError when the CUDA
+    library has not been built."""
     global _lib
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"CUDA library {LIB_PATH} is missing: run paper_1910_13844_gb300.build.build() "
-                          "(there is no CPU fallback)")
+        raise ImportError(f"CUDA library {LIB_PATH} is missing: run paper_1910_13844_gb300.build.build("
+                          f"{'debug=True' if DEBUG_BOUNDS else ''}) (there is no CPU fallback)")
     lib = C.CDLL(LIB_PATH)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)

@@ -303,6 +303,7 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   Engine& e = P->eng;
   FxParams fx = fx_in;
   fx.sel = counted(P, fx.sel, LS_K_FX);
+  fx.dbg_probe = P->inj_bounds_probe;
   timed(P, LS_K_FX, nslots, st, [&] { P->px.fx(fx, nslots, st); });
   StridedParams fy = fy_base(P, counted(P, sel, LS_K_FY), e.a1, e.a1_stride, e.a2, e.a2_stride, P->nz);
   timed(P, LS_K_FY, nslots, st, [&] { P->py.fy(fy, nslots, st); });
@@ -335,6 +336,7 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   ix.src = e.a1; ix.src_stride = e.a1_stride;
   ix.tw2 = P->tw2_x;
   ix.prefetch = P->tune_ix_prefetch;
+  ix.maxparts = e.maxparts;
   timed(P, LS_K_IX, nslots, st, [&] { P->px.ix(ix, nslots, st); });
 }
 
@@ -422,6 +424,7 @@ void seq_iter(ls_plan* P, int nslots, cudaStream_t st) {
     u.x = e.vptr(V_X); u.r = e.vptr(V_R);
     u.p = e.vptr(V_P); u.s = e.vptr(V_S); u.t = e.vptr(V_T); u.rh = e.vptr(V_RH);
     u.partials = e.partials;
+    u.maxparts = e.maxparts;
     const int nb = upd_blocks(P, nslots);
     timed(P, LS_K_UPDATE, nslots, st, [&] { launch_update(u, nb, nslots, st); });
     ScalarParams sc{e.slots_d, SLOT_ITER, PH_RHO, e.partials, nb};
@@ -563,6 +566,7 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   v.device = P->device; v.sms = P->sms;
   v.tune_z_tma = P->tune_z_tma; v.tune_ix_prefetch = P->tune_ix_prefetch;
   v.tune_fx_views_fastest = P->tune_fx_views_fastest;
+  v.inj_z_stall = P->inj_z_stall; v.inj_z_wait_ns = P->inj_z_wait_ns; v.inj_bounds_probe = P->inj_bounds_probe;
   const Engine& e = P->eng;
   Engine& w = v.eng;
   w = e;
@@ -634,6 +638,7 @@ int tune_forward(ls_plan* P, const float* f, int n, cudaStream_t st) {
 }
 
 int engine_solve(ls_plan* P, int nslots, cudaStream_t st) {
+  TraceRange range("solve");
   Engine& e = P->eng;
   LS_CUDA_TRY(cudaMemcpyAsync(e.slots_d, e.slots_h, (size_t)nslots * sizeof(SlotDev), cudaMemcpyHostToDevice, st));
   // the z pass's error word (a TMA wait that gave up) covers this solve only
@@ -837,6 +842,7 @@ size_t ls_workspace_bytes(const ls_grid* g, int n_views) {
 
 int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel, const ls_options* opt,
                    ls_plan** out) {
+  lsgpu::TraceRange trace_range("ls_plan_create");
   if (!grid || !out) { set_last_error("null argument"); return LS_EINVAL; }
   *out = nullptr;
   if (padding != 2) { set_last_error("storage padding must be 2 (Prop. 1)"); return LS_EINVAL; }
@@ -951,6 +957,7 @@ void ls_plan_destroy(ls_plan* P) {
 }
 
 int ls_green_spectrum(ls_plan* P, int p, ls_c64* out_full, void* stream) {
+  lsgpu::TraceRange trace_range("ls_green_spectrum");
   if (!P) { set_last_error("null plan"); return LS_EINVAL; }
   if (p < 2 || (p & 1)) { set_last_error("oversampling p must be even and >= 2"); return LS_EINVAL; }
   cudaStream_t st = (cudaStream_t)stream;
@@ -996,6 +1003,7 @@ int ls_scattering_potential(const float* dn, size_t count, double eta_b, double 
 }
 
 int ls_plane_waves(ls_plan* P, int n_views, const double* kvec, ls_c64* const* u_in, void* stream) {
+  lsgpu::TraceRange trace_range("ls_plane_waves");
   if (!P || !kvec || !u_in || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
   for (int q = 0; q < n_views; ++q) if (!u_in[q]) { set_last_error("u_in[%d] is null", q); return LS_EINVAL; }
   cudaStream_t st = (cudaStream_t)stream;
@@ -1032,11 +1040,13 @@ static int single_op(ls_plan* P, const float* f, const ls_c64* x, ls_c64* y, int
 }
 
 int ls_apply_green(ls_plan* P, const ls_c64* v, ls_c64* out, int adjoint, void* stream) {
+  lsgpu::TraceRange trace_range("ls_apply_green");
   if (!P || !v || !out) { set_last_error("bad arguments"); return LS_EINVAL; }
   return single_op(P, nullptr, v, out, adjoint, 0, (cudaStream_t)stream);
 }
 
 int ls_matvec(ls_plan* P, const float* f, const ls_c64* x, ls_c64* y, int adjoint, void* stream) {
+  lsgpu::TraceRange trace_range("ls_matvec");
   if (!P || !f || !x || !y) { set_last_error("bad arguments"); return LS_EINVAL; }
   return single_op(P, f, x, y, adjoint, 1, (cudaStream_t)stream);
 }
@@ -1054,6 +1064,7 @@ static int check_views(int n, const void* const* a, const char* what, bool allow
 
 int ls_matvec_batch(ls_plan* P, const float* f, int n_views, const ls_c64* const* x, ls_c64* const* y, int adjoint,
                     void* stream) {
+  lsgpu::TraceRange trace_range("ls_matvec_batch");
   if (!P || !f || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
   int rc = check_views(n_views, (const void* const*)x, "x", false);
   if (!rc) rc = check_views(n_views, (const void* const*)y, "y", false);
@@ -1175,16 +1186,19 @@ static int forward_impl(ls_plan* P, const float* f, int n_views, const ls_c64* c
 
 int ls_forward(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_in, ls_c64* const* u_out,
                ls_c64* const* far, ls_stats* stats, void* stream) {
+  lsgpu::TraceRange trace_range("ls_forward");
   return forward_impl(P, f, n_views, u_in, nullptr, u_out, far, stats, stream);
 }
 
 int ls_forward_warm(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_in, const ls_c64* const* x0,
                     ls_c64* const* u_out, ls_c64* const* far, ls_stats* stats, void* stream) {
+  lsgpu::TraceRange trace_range("ls_forward_warm");
   if (!x0) { set_last_error("x0 is null (use ls_forward)"); return LS_EINVAL; }
   return forward_impl(P, f, n_views, u_in, x0, u_out, far, stats, stream);
 }
 
 int ls_farfield(ls_plan* P, const float* f, int n_views, const ls_c64* const* u, ls_c64* const* far, void* stream) {
+  lsgpu::TraceRange trace_range("ls_farfield");
   if (!P || !f || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
   int rc = check_views(n_views, (const void* const*)u, "u", false);
   if (!rc) rc = check_views(n_views, (const void* const*)far, "far", false);
@@ -1209,6 +1223,7 @@ int ls_farfield(ls_plan* P, const float* f, int n_views, const ls_c64* const* u,
 }
 
 int ls_farfield_adjoint(ls_plan* P, int n_views, const ls_c64* const* r, ls_c64* const* out, void* stream) {
+  lsgpu::TraceRange trace_range("ls_farfield_adjoint");
   if (!P || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
   int rc = check_views(n_views, (const void* const*)r, "r", false);
   if (!rc) rc = check_views(n_views, (const void* const*)out, "out", false);
@@ -1233,6 +1248,7 @@ int ls_farfield_adjoint(ls_plan* P, int n_views, const ls_c64* const* r, ls_c64*
 
 int ls_residual(int n_views, size_t count, const ls_c64* const* pred, const ls_c64* const* meas, ls_c64* const* res,
                 double* loss_out, void* stream) {
+  lsgpu::TraceRange trace_range("ls_residual");
   if (n_views < 1 || count == 0) { set_last_error("bad arguments"); return LS_EINVAL; }
   int rc = check_views(n_views, (const void* const*)pred, "pred", false);
   if (!rc) rc = check_views(n_views, (const void* const*)meas, "meas", false);
@@ -1272,6 +1288,7 @@ int ls_residual(int n_views, size_t count, const ls_c64* const* pred, const ls_c
 
 int ls_inner_products(int n_views, size_t count, const ls_c64* const* a, const ls_c64* const* b, double* out,
                       void* stream) {
+  lsgpu::TraceRange trace_range("ls_inner_products");
   if (n_views < 1 || count == 0 || !out) { set_last_error("bad arguments"); return LS_EINVAL; }
   int rc = check_views(n_views, (const void* const*)a, "a", false);
   if (!rc) rc = check_views(n_views, (const void* const*)b, "b", false);
@@ -1311,6 +1328,7 @@ int ls_inner_products(int n_views, size_t count, const ls_c64* const* a, const l
 int ls_gradient(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_in, const ls_c64* const* u_fwd,
                 const ls_c64* const* residuals, const double* view_weights, float* grad, ls_stats* stats,
                 void* stream) {
+  lsgpu::TraceRange trace_range("ls_gradient");
   if (!P || !f || !grad || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
   int rc = check_views(n_views, (const void* const*)residuals, "residuals", false);
   if (!rc && !u_fwd) rc = check_views(n_views, (const void* const*)u_in, "u_in", true);
@@ -1367,6 +1385,30 @@ int ls_gradient(ls_plan* P, const float* f, int n_views, const ls_c64* const* u_
   return adj_status;
 }
 
+int ls_debug_bounds(unsigned* site, int clear) {
+  if (site) *site = 0;
+#ifdef LS_DEBUG_BOUNDS
+  unsigned (*const readers[])(bool) = {bounds_site_16,  bounds_site_24,  bounds_site_32,  bounds_site_48,
+                                       bounds_site_64,  bounds_site_96,  bounds_site_128, bounds_site_144,
+                                       bounds_site_192, bounds_site_256, bounds_site_288, bounds_site_384,
+                                       bounds_site_krylov};
+  unsigned first = 0;
+  for (auto rd : readers) {
+    const unsigned v = rd(clear != 0);
+    if (v == 0xffffffffu) {
+      set_last_error("ls_debug_bounds: an index-check record could not be read");
+      return LS_ECUDA;
+    }
+    if (first == 0) first = v;
+  }
+  if (site) *site = first;
+  return 1;
+#else
+  (void)clear;
+  return 0;
+#endif
+}
+
 int ls_debug_inject(ls_plan* P, int kind, long long value) {
   switch (kind) {
     case LS_INJECT_NONE:
@@ -1375,6 +1417,7 @@ int ls_debug_inject(ls_plan* P, int kind, long long value) {
       P->inj_max_rounds = -1;
       P->inj_z_stall = 0;
       P->inj_z_wait_ns = 0;
+      P->inj_bounds_probe = 0;
       g_fail_allocs.store(0);
       return LS_OK;
     case LS_INJECT_ZERO_SHADOW:
@@ -1393,6 +1436,10 @@ int ls_debug_inject(ls_plan* P, int kind, long long value) {
       if (value < 0) { set_last_error("wait limit must be >= 0"); return LS_EINVAL; }
       P->inj_z_stall = value > 0 ? 1 : 0;
       P->inj_z_wait_ns = value;
+      return LS_OK;
+    case LS_INJECT_BOUNDS_PROBE:
+      if (!P) { set_last_error("null plan"); return LS_EINVAL; }
+      P->inj_bounds_probe = value != 0 ? 1 : 0;
       return LS_OK;
     default:
       set_last_error("unknown injection kind %d", kind);

@@ -120,6 +120,7 @@ static double time_ms(cudaStream_t st, int reps, F fn) {
 using namespace lsgpu;
 
 extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out, void* stream) {
+  lsgpu::TraceRange trace_range("ls_autotune");
   if (!P || !f || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
   cudaStream_t st = (cudaStream_t)stream;
   const std::string key = tune_key(P, n_views);

@@ -9,6 +9,7 @@
 #include "green.cuh"
 #include "krylov.cuh"
 #include "passes.cuh"
+#include "trace.h"
 
 namespace lsgpu {
 
@@ -87,6 +88,7 @@ struct ls_plan {
   long long inj_max_rounds = -1;  // host rounds a solve may take (-1: the normal bound)
   int inj_z_stall = 0;            // the TMA-staged z pass waits on a barrier nothing completes
   long long inj_z_wait_ns = 0;    // per-view wait limit of the TMA-staged z pass (0: one second)
+  int inj_bounds_probe = 0;       // debug build: the first pass treats its last view as out of range
   // ls_matvec_noalloc: device address of the library's static scratch array on this plan's device,
   // looked up when the plan is created (null, with noalloc_rc set, if that failed)
   int device = 0;
@@ -134,12 +136,14 @@ int apply_pupil_device(ls_plan* P, const float2* in, float2* out, int adjoint, d
 // current device; loads the array's module (reserving the array) if that has not happened yet.
 int noalloc_setup(void** addr);
 
-// Launch wrapper: when profiling is on, bracket the launch with an event pair.
+// Launch wrapper: an NVTX range named after the kind; when profiling is on, the launch is also
+// bracketed with an event pair.
 cudaEvent_t prof_event(ls_plan* P);
 void prof_resolve(ls_plan* P, bool wait);
 inline ls_plan* prof_owner(ls_plan* P) { return P->prof_parent ? P->prof_parent : P; }
 template <class F>
 inline void timed(ls_plan* P0, int kind, int nslots, cudaStream_t st, F&& launch) {
+  TraceRange range(trace_kind_name(kind));
   ls_plan* P = prof_owner(P0);
   if (!P->prof.on) {
     launch();

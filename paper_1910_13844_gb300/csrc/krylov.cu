@@ -22,6 +22,7 @@ namespace lsgpu {
 // x += alpha p + omega s ; r = s - omega t ; partials <rh, r>, ||r||^2
 __global__ void __launch_bounds__(256, 4) k_update(UpdParams a) {
   const int slot = blockIdx.y;
+  if (!LS_IN_BOUNDS(slot < a.sel.nslots && (a.sel.nslots <= 1 || a.n <= a.vstride), BS_UPD_VEC)) return;
   if (!slot_runs(a.sel, slot)) return;
   count_run(a.sel);
   const SlotDev& sd = a.sel.slots[slot];
@@ -53,7 +54,8 @@ __global__ void __launch_bounds__(256, 4) k_update(UpdParams a) {
     acc[1] += d0.y + d1.y;
     acc[2] += r0.x * r0.x + r0.y * r0.y + r1.x * r1.x + r1.y * r1.y;
   }
-  block_sum_store<3>(acc, a.partials + ((size_t)slot * gridDim.x + blockIdx.x) * 4);
+  if (LS_IN_BOUNDS(a.maxparts == 0 || (int)gridDim.x <= a.maxparts, BS_UPD_PART))
+    block_sum_store<3>(acc, a.partials + ((size_t)slot * gridDim.x + blockIdx.x) * 4);
 }
 
 // ------------------------------------------------------------------ scalar steps
@@ -334,7 +336,9 @@ __global__ void __launch_bounds__(256) k_inner(ResidualParams a) {
 }
 
 // ------------------------------------------------------------------ launchers
-void launch_update(const UpdParams& a, int nblocks, int nslots, cudaStream_t st) {
+void launch_update(const UpdParams& a0, int nblocks, int nslots, cudaStream_t st) {
+  UpdParams a = a0;
+  a.sel.nslots = nslots;
   k_update<<<dim3(nblocks, nslots), 256, 0, st>>>(a);
 }
 void launch_scalar(const ScalarParams& a, int nslots, cudaStream_t st) {
@@ -393,5 +397,7 @@ void launch_inner(const ResidualParams& a, int nblocks, int nviews, cudaStream_t
 void launch_residual(const ResidualParams& a, int nblocks, int nviews, cudaStream_t st) {
   k_residual<<<dim3(nblocks, nviews), 256, 0, st>>>(a);
 }
+
+LS_BOUNDS_READER(krylov)
 
 }  // namespace lsgpu

@@ -8,12 +8,16 @@ namespace lsgpu {
 
 enum ScalarPhase : int { PH_RESID = 0, PH_ALPHA = 1, PH_OMEGA = 2, PH_RHO = 3 };
 
+// debug build: the index-check record of krylov.cu (debug_bounds.cuh)
+unsigned bounds_site_krylov(bool clear);
+
 struct UpdParams {
   SlotSel sel;
   size_t n, vstride;
   float2 *x, *r;
   const float2 *p, *s, *t, *rh;
   double* partials;
+  int maxparts = 0;   // partial-sum blocks allocated per slot (0: not checked)
 };
 
 struct ScalarParams {

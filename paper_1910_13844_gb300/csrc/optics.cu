@@ -150,6 +150,7 @@ extern "C" {
 
 int ls_incident_field(ls_plan* P, int n_views, const ls_c64* const* y_in, const double* k_in,
                       ls_c64* const* u_in, void* stream) {
+  lsgpu::TraceRange trace_range("ls_incident_field");
   if (!P || n_views < 1 || !y_in || !u_in) { set_last_error("bad arguments"); return LS_EINVAL; }
   for (int q = 0; q < n_views; ++q)
     if (!y_in[q] || !u_in[q]) { set_last_error("null view pointer %d", q); return LS_EINVAL; }
@@ -196,6 +197,7 @@ int ls_set_pupil(ls_plan* P, double k_cut, double distance) {
 }
 
 int ls_apply_pupil(ls_plan* P, int n_views, const ls_c64* const* in, ls_c64* const* out, int adjoint, void* stream) {
+  lsgpu::TraceRange trace_range("ls_apply_pupil");
   if (!P || n_views < 1 || !in || !out) { set_last_error("bad arguments"); return LS_EINVAL; }
   if (!P->pupil_h) { set_last_error("no pupil set (ls_set_pupil)"); return LS_EINVAL; }
   cudaStream_t st = (cudaStream_t)stream;

@@ -5,6 +5,7 @@
 #include <cuda.h>   // CUtensorMap (the tensor map is encoded on the host through the runtime's driver entry point)
 
 #include "common.cuh"
+#include "debug_bounds.cuh"
 #include "dft.cuh"
 
 namespace lsgpu {
@@ -40,6 +41,7 @@ struct FxParams {
   int bulk = 0;                // bulk-copy-staged persistent variant in the BiCGStab modes (autotuned)
   int sms = 0;                 // SMs of the device (grid of the bulk-staged variant)
   int* err = nullptr;          // set to 1 if a wait for a bulk copy gave up (bulk-staged variant)
+  int dbg_probe = 0;           // debug build, test only: the plain kernel's slot check excludes the last slot
 };
 
 struct StridedParams {
@@ -86,9 +88,16 @@ struct IxParams {
   size_t vstride;              // slot stride for in*/out* (STORE: stride of out0)
   int out_o, out_m;            // STORE: output window [out_o, out_o+out_m) of x; out rows are out_m long
   double* partials;            // [slot][gridDim.x][4]
+  int maxparts = 0;            // partial-sum blocks allocated per slot (0: not checked)
   const float2* tw2;
   int prefetch = 0;            // ask L2 for the epilogue operands at kernel start (autotuned)
 };
+
+// Debug-build index check: element `off` of slot `slot` of a [slots][stride] array whose slots
+// hold `extent` elements each (stride 0 or unused when the launch covers one slot).
+__device__ __forceinline__ bool slot_elem_ok(int slot, int nslots, size_t off, size_t extent, size_t stride) {
+  return slot >= 0 && slot < nslots && off < extent && (nslots <= 1 || extent <= stride);
+}
 
 __device__ __forceinline__ bool slot_runs(const SlotSel& s, int slot) {
   return !(s.slots && s.mask && !(s.slots[slot].flags & s.mask));

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 6) k_fx(FxParams a) {
   // common to the views of one sample) run together and f is read from L2
   const int slot = a.views_fastest ? blockIdx.x : blockIdx.y;
   const int rb = a.views_fastest ? blockIdx.y : blockIdx.x;
+  if (!LS_IN_BOUNDS(slot < a.sel.nslots - (a.dbg_probe ? 1 : 0), BS_SLOT)) return;
   if (!slot_runs(a.sel, slot)) return;
   count_run_if(a.sel, rb == 0);
   const int t = threadIdx.x, p = threadIdx.y;
@@ -96,6 +97,9 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 6) k_fx(FxParams a) {
     for (int n1 = 0; n1 < R1 / 2; ++n1) {
       const int x = R2 * n1 + t;
       const size_t i = voff + x;
+      if (!LS_IN_BOUNDS(slot_elem_ok(slot, a.sel.nslots, (size_t)row * nx + x, (size_t)a.rows * nx, a.vstride),
+                        BS_FX_VEC))
+        continue;
       float2 val = __ldg(a.src + i);
       if (a.mode == FX_BICG_P) {
         if (!first) {
@@ -134,7 +138,10 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 6) k_fx(FxParams a) {
     Dft<R2, -1>::run(u);
     float2* d = a.dst + (size_t)slot * a.dst_stride + (size_t)row * L;
 #pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) d[t + R1 * k2] = u[k2];
+    for (int k2 = 0; k2 < R2; ++k2)
+      if (LS_IN_BOUNDS(slot_elem_ok(slot, a.sel.nslots, (size_t)row * L + t + R1 * k2, (size_t)a.rows * L,
+                                    a.dst_stride), BS_FX_DST))
+        d[t + R1 * k2] = u[k2];
   }
 }
 
@@ -193,6 +200,12 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 1) k_fxb(FxParams a) {
     const int nrows = min(PC, a.rows - row0);
     const unsigned vb = (unsigned)(nrows * NX * sizeof(float2));
     const size_t voff = (size_t)slot * a.vstride + (size_t)row0 * NX;
+    if (!LS_IN_BOUNDS(slot < a.sel.nslots && row0 >= 0 && row0 + nrows <= a.rows &&
+                          (a.sel.nslots <= 1 || (size_t)a.rows * NX <= a.vstride), BS_FXB_COPY)) {
+      s_fb[s] = 0;
+      mbar_arrive(&full[s]);   // nothing copied: the stage's phase completes at once
+      return;
+    }
     const float* f = a.mode == FX_COPY ? nullptr : slot_f(a.sel, slot) + (size_t)row0 * NX;
     const bool fb = f && ((reinterpret_cast<uintptr_t>(f) & 15) == 0);
     s_fb[s] = fb ? 1 : 0;
@@ -254,6 +267,10 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 1) k_fxb(FxParams a) {
 #pragma unroll
       for (int n1 = 0; n1 < R1 / 2; ++n1) {
         const int x = R2 * n1 + t;
+        if (!LS_IN_BOUNDS(x < NX && p < PC, BS_FXB_SMEM) ||
+            !LS_IN_BOUNDS(slot_elem_ok(slot, a.sel.nslots, (size_t)row * NX + x, (size_t)a.rows * NX, a.vstride),
+                          BS_FX_VEC))
+          continue;
         float2 val = r_s[x];
         if (a.mode == FX_BICG_P) {
           if (!first) {
@@ -289,7 +306,10 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 1) k_fxb(FxParams a) {
       Dft<R2, -1>::run(u);
       float2* d = a.dst + (size_t)slot * a.dst_stride + (size_t)row * L;
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) d[t + R1 * k2] = u[k2];
+      for (int k2 = 0; k2 < R2; ++k2)
+        if (LS_IN_BOUNDS(slot_elem_ok(slot, a.sel.nslots, (size_t)row * L + t + R1 * k2, (size_t)a.rows * L,
+                                      a.dst_stride), BS_FX_DST))
+          d[t + R1 * k2] = u[k2];
     }
     __syncthreads();   // the exchange area is free for the next item
   }
@@ -305,6 +325,7 @@ __global__ void __launch_bounds__(Geo<L>::T * P) k_strided(StridedParams a) {
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
   const int slot = blockIdx.y;
+  if (!LS_IN_BOUNDS(slot < a.sel.nslots, BS_SLOT)) return;
   if (!slot_runs(a.sel, slot)) return;
   count_run(a.sel);
   const int p = threadIdx.x, t = threadIdx.y;
@@ -313,6 +334,11 @@ __global__ void __launch_bounds__(Geo<L>::T * P) k_strided(StridedParams a) {
   const int c = (blockIdx.x % tiles_c) * P + p;
   const bool valid = c < a.ncont;
   const float2* src = a.src + (size_t)slot * a.src_stride + (size_t)plane * a.src_plane + c;
+  // debug build: a slot's extent in the source (FY reads L/2 rows of a plane, IY all L) and the
+  // destination (FY writes L rows, IY the out_m rows of its window)
+  const size_t src_ext = (size_t)(a.planes - 1) * a.src_plane + (size_t)(DIR < 0 ? L / 2 : L) * a.ncont;
+  const size_t dst_ext = (size_t)(a.planes - 1) * a.dst_plane + (size_t)(DIR < 0 ? L : a.out_m) * a.ncont;
+  (void)src_ext; (void)dst_ext;
   float2 v[R1];
 #pragma unroll
   for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
@@ -320,7 +346,10 @@ __global__ void __launch_bounds__(Geo<L>::T * P) k_strided(StridedParams a) {
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
       const int y = R2 * n1 + t;
-      if (DIR < 0 ? (n1 < R1 / 2) : true) v[n1] = __ldg(src + (size_t)y * a.ncont);
+      if ((DIR < 0 ? (n1 < R1 / 2) : true) &&
+          LS_IN_BOUNDS(slot_elem_ok(slot, a.sel.nslots, (size_t)plane * a.src_plane + (size_t)y * a.ncont + c,
+                                    src_ext, a.src_stride), BS_ST_SRC))
+        v[n1] = __ldg(src + (size_t)y * a.ncont);
     }
   }
   if (t < R2) {
@@ -331,7 +360,8 @@ __global__ void __launch_bounds__(Geo<L>::T * P) k_strided(StridedParams a) {
       v[k1] = DIR < 0 ? cmul(v[k1], w) : cmulc(v[k1], w);
     }
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) sm[(k1 * R2 + t) * P + p] = v[k1];
+    for (int k1 = 0; k1 < R1; ++k1)
+      if (LS_IN_BOUNDS((k1 * R2 + t) * P + p < L * P, BS_ST_SMEM)) sm[(k1 * R2 + t) * P + p] = v[k1];
   }
   __syncthreads();
   if (valid && t < R1) {
@@ -342,13 +372,20 @@ __global__ void __launch_bounds__(Geo<L>::T * P) k_strided(StridedParams a) {
     float2* dst = a.dst + (size_t)slot * a.dst_stride + (size_t)plane * a.dst_plane + c;
     if (DIR < 0) {
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) dst[(size_t)(t + R1 * k2) * a.ncont] = u[k2];
+      for (int k2 = 0; k2 < R2; ++k2)
+        if (LS_IN_BOUNDS(slot_elem_ok(slot, a.sel.nslots,
+                                      (size_t)plane * a.dst_plane + (size_t)(t + R1 * k2) * a.ncont + c,
+                                      dst_ext, a.dst_stride), BS_ST_DST))
+          dst[(size_t)(t + R1 * k2) * a.ncont] = u[k2];
     } else {
 #pragma unroll
       for (int k2 = 0; k2 < R2 / 2; ++k2) {
         const int y = t + R1 * k2;
         const int yo = y - a.out_o;
-        if (yo >= 0 && yo < a.out_m) dst[(size_t)yo * a.ncont] = u[k2];
+        if (yo >= 0 && yo < a.out_m &&
+            LS_IN_BOUNDS(slot_elem_ok(slot, a.sel.nslots, (size_t)plane * a.dst_plane + (size_t)yo * a.ncont + c,
+                                      dst_ext, a.dst_stride), BS_ST_DST))
+          dst[(size_t)yo * a.ncont] = u[k2];
       }
     }
   }
@@ -365,6 +402,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
   const int slot = blockIdx.y;
+  if (!LS_IN_BOUNDS(slot < a.sel.nslots, BS_SLOT)) return;
   if (!slot_runs(a.sel, slot)) return;
   count_run(a.sel);
   const int t = threadIdx.x, p = threadIdx.y;
@@ -385,7 +423,10 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
   if (valid && t < R2) {
     const float2* s = a.src + (size_t)slot * a.src_stride + (size_t)row * L;
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(s + R2 * n1 + t);
+    for (int n1 = 0; n1 < R1; ++n1)
+      if (LS_IN_BOUNDS(slot_elem_ok(slot, a.sel.nslots, (size_t)row * L + R2 * n1 + t, (size_t)a.rows * L,
+                                    a.src_stride), BS_IX_SRC))
+        v[n1] = __ldg(s + R2 * n1 + t);
   }
   float2* S = sm + (size_t)p * R1 * G::SROW;
   if (t < R2) {
@@ -408,10 +449,17 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
       const int x = t + R1 * k2;
       const float2 g = u[k2];
       const size_t i = voff + x;
+      if (!LS_IN_BOUNDS(a.mode == IX_STORE ||
+                            slot_elem_ok(slot, a.sel.nslots, (size_t)row * nx + x, (size_t)a.rows * nx, a.vstride),
+                        BS_IX_VEC))
+        continue;
       switch (a.mode) {
         case IX_STORE: {
           const int xo = x - a.out_o;
-          if (xo >= 0 && xo < a.out_m) a.out0[(size_t)slot * a.vstride + (size_t)row * a.out_m + xo] = g;
+          if (xo >= 0 && xo < a.out_m &&
+              LS_IN_BOUNDS(slot_elem_ok(slot, a.sel.nslots, (size_t)row * a.out_m + xo, (size_t)a.rows * a.out_m,
+                                        a.vstride), BS_IX_VEC))
+            a.out0[(size_t)slot * a.vstride + (size_t)row * a.out_m + xo] = g;
         } break;
         case IX_MATVEC:
           a.out0[i] = csub(__ldg(a.in0 + i), g);
@@ -442,7 +490,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
       }
     }
   }
-  if (a.mode >= IX_BICG_V) {
+  if (a.mode >= IX_BICG_V && LS_IN_BOUNDS(a.maxparts == 0 || (int)gridDim.x <= a.maxparts, BS_IX_PART)) {
     block_sum_store<3>(acc, a.partials + ((size_t)slot * gridDim.x + blockIdx.x) * 4);
   }
 }
@@ -481,14 +529,20 @@ struct PassImpl {
     }
     const unsigned rbs = (unsigned)((a.rows + G::PC - 1) / G::PC);
     dim3 blk(G::T, G::PC), grd = a.views_fastest ? dim3(nslots, rbs) : dim3(rbs, nslots);
-    k_fx<L><<<grd, blk, G::smem_contig, st>>>(a);
+    FxParams b = a;
+    b.sel.nslots = nslots;
+    k_fx<L><<<grd, blk, G::smem_contig, st>>>(b);
   }
-  static void ix(const IxParams& a, int nslots, cudaStream_t st) {
+  static void ix(const IxParams& a0, int nslots, cudaStream_t st) {
+    IxParams a = a0;
+    a.sel.nslots = nslots;
     dim3 blk(G::T, G::PC), grd((a.rows + G::PC - 1) / G::PC, nslots);
     k_ix<L><<<grd, blk, G::smem_contig, st>>>(a);
   }
   template <int DIR>
-  static void strided(const StridedParams& a, int nslots, cudaStream_t st) {
+  static void strided(const StridedParams& a0, int nslots, cudaStream_t st) {
+    StridedParams a = a0;
+    a.sel.nslots = nslots;
     if (a.wide && G::T * 32 <= 1024) {
       constexpr int W = G::T * 32 <= 1024 ? 32 : 16;
       dim3 blk(W, G::T), grd(((a.ncont + W - 1) / W) * a.planes, nslots);
@@ -594,7 +648,8 @@ struct PassImpl {
 // Defined in one translation unit per length (passes_L*.cu).
 #define LS_DECLARE_LENGTH(L) \
   PassLaunch pass_table_##L(); \
-  cudaError_t pass_setup_##L();
+  cudaError_t pass_setup_##L(); \
+  unsigned bounds_site_##L(bool clear);
 LS_DECLARE_LENGTH(16)
 LS_DECLARE_LENGTH(24)
 LS_DECLARE_LENGTH(32)
@@ -611,6 +666,7 @@ LS_DECLARE_LENGTH(384)
 
 #define LS_DEFINE_LENGTH(L) \
   PassLaunch pass_table_##L() { return PassImpl<L>::table(); } \
-  cudaError_t pass_setup_##L() { return PassImpl<L>::setup(); }
+  cudaError_t pass_setup_##L() { return PassImpl<L>::setup(); } \
+  LS_BOUNDS_READER(L)
 
 }  // namespace lsgpu

@@ -375,6 +375,7 @@ struct ls_server {
 
   // -------------------------------------------------------------- one round over the lanes
   void issue(Lane* l) {
+    TraceRange range("serve_round");
     ls_plan* P = l->plan;
     Engine& e = P->eng;
     cudaStream_t st = l->stream;
@@ -494,6 +495,7 @@ int ls_server_create(const ls_server_options* opt, ls_server** out) {
 }
 
 int ls_submit(ls_server* S, const ls_request* req, uint64_t* ticket) {
+  lsgpu::TraceRange trace_range("ls_submit");
   if (!S || !req || !ticket) { set_last_error("null argument"); return LS_EINVAL; }
   if (req->n_views < 1 || !req->f || !req->kvec) { set_last_error("request needs n_views >= 1, f and kvec"); return LS_EINVAL; }
   if (req->kind != LS_REQ_FORWARD && req->kind != LS_REQ_GRADIENT) { set_last_error("unknown request kind"); return LS_EINVAL; }

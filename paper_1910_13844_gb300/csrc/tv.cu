@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "trace.h"
 
 namespace lsgpu {
 
@@ -82,6 +83,7 @@ using namespace lsgpu;
 
 extern "C" int ls_prox_tv(const ls_grid* grid, const float* z, float* x, double lam, int iters, float* work,
                           void* stream) {
+  lsgpu::TraceRange trace_range("ls_prox_tv");
   if (!grid || !z || !x || grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || iters < 0) {
     set_last_error("bad arguments");
     return LS_EINVAL;

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PS, Geo<L>::ZMINB) k_z(ZPa
   }
   // staging of one view: NZ rows of P complex values, as 16-byte pairs
   auto stage_view = [&](int slot, float2* buf) {
+    if (!LS_IN_BOUNDS(slot < a.sel.nslots, BS_SLOT)) return;
     const float2* base = a.a2 + (size_t)slot * a.a2_stride + (size_t)ky * ncont + kx0;
     for (int c = tid; c < NZ * (P / 2); c += NT) {
       const int z = c / (P / 2), j = 2 * (c % (P / 2));
@@ -283,7 +284,9 @@ __device__ __forceinline__ void load_green(float2 (&g)[R2], const ZParams& a, in
 #pragma unroll
   for (int k2 = 0; k2 < R2; ++k2) {
     const int kz = k2 < R2 / 2 ? t + R1 * k2 : L - R1 * k2 - t;
-    g[k2] = __ldg(col + (size_t)kz * plane);
+    g[k2] = LS_IN_BOUNDS(kz >= 0 && kz <= a.nz && fy >= 0 && fy <= a.ny && fx >= 0 && fx <= a.nx, BS_Z_GREEN)
+                ? __ldg(col + (size_t)kz * plane)
+                : make_float2(0.f, 0.f);
   }
 }
 
@@ -332,6 +335,10 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
   // TMA coordinates of the item (view position iv, tile number kt of this CTA): (2 kx0 floats, ky, 0, slot)
   auto item_load = [&](int iv, int kt, int buf) {
     const int j = (int)blockIdx.x + kt * (int)gridDim.x;
+    if (!LS_IN_BOUNDS(j < ntiles && iv < nact && active_slot(s_list[iv]) < a.sel.nslots, BS_Z_TILE)) {
+      mbar_arrive(&full[buf]);   // nothing copied: the buffer's phase completes at once
+      return;
+    }
     mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
     tma_load_4d(stage + (size_t)buf * NZ * P, &a.tmap, &full[buf], 2 * (j % tiles_c) * P, j / tiles_c, 0,
                 a.slot0 + active_slot(s_list[iv]));
@@ -353,7 +360,8 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
     for (int i = tid; i < (NZ + 1) * P; i += W::NT) {
       const int kz = i / P, cc = i % P, kx = kx0 + cc;
       const int fx = kx <= a.nx ? kx : 2 * a.nx - kx;
-      gs[kz * W::GR + cc] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+      if (LS_IN_BOUNDS(kz <= a.nz && fy >= 0 && fy <= a.ny && fx >= 0 && fx <= a.nx, BS_Z_GREEN))
+        gs[kz * W::GR + cc] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
     }
   }
   for (int i = tid; i < R1 * R2; i += W::NT) {
@@ -372,8 +380,9 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
       const int buf = i % NS;
       if (!mbar_wait_abort(&done[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZW_LIMIT)) break;
       const int j = (int)blockIdx.x + skt * (int)gridDim.x;
-      tma_store_4d(&a.tmap, stage + (size_t)buf * NZ * P, 2 * (j % tiles_c) * P, j / tiles_c, 0,
-                   a.slot0 + active_slot(s_list[sv]));
+      if (LS_IN_BOUNDS(j < ntiles && active_slot(s_list[sv]) < a.sel.nslots, BS_Z_TILE))
+        tma_store_4d(&a.tmap, stage + (size_t)buf * NZ * P, 2 * (j % tiles_c) * P, j / tiles_c, 0,
+                     a.slot0 + active_slot(s_list[sv]));
       bulk_commit();
       if (i + NS < nitems) {
         bulk_wait_read_all();   // the store has read the buffer
@@ -431,8 +440,11 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
 #pragma unroll
       for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int n1 = 0; n1 < R1 / 2; ++n1)
-        v[n1] = *reinterpret_cast<const float2*>(sb + (R2 % 8 == 0 ? rb + R2 * n1 * 128 : swz128(R2 * n1 + t, c)));
+      for (int n1 = 0; n1 < R1 / 2; ++n1) {
+        const unsigned off = R2 % 8 == 0 ? rb + R2 * n1 * 128 : swz128(R2 * n1 + t, c);
+        if (LS_IN_BOUNDS(off + sizeof(float2) <= W::stage_bytes, BS_Z_SMEM))
+          v[n1] = *reinterpret_cast<const float2*>(sb + off);
+      }
       Dft<R1, -1, R1 / 2, R1>::run(v);
       const float4* tw4 = reinterpret_cast<const float4*>(twa + t * W::TWA);
 #pragma unroll
@@ -442,7 +454,8 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
         v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
       }
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) xc[k1 * (R2 + 2) + t] = v[k1];
+      for (int k1 = 0; k1 < R1; ++k1)
+        if (LS_IN_BOUNDS(c * W::XP + k1 * (R2 + 2) + t < P * W::XP, BS_Z_SMEM)) xc[k1 * (R2 + 2) + t] = v[k1];
     }
     __syncwarp();
     if (stage2_thread) {
@@ -501,8 +514,11 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
       Dft<R1, +1, R1, R1 / 2>::run(w);
       // outputs z = t + R2 j2 (j2 < R1/2: z < nz), in place
 #pragma unroll
-      for (int j2 = 0; j2 < R1 / 2; ++j2)
-        *reinterpret_cast<float2*>(sb + (R2 % 8 == 0 ? rb + R2 * j2 * 128 : swz128(t + R2 * j2, c))) = w[j2];
+      for (int j2 = 0; j2 < R1 / 2; ++j2) {
+        const unsigned off = R2 % 8 == 0 ? rb + R2 * j2 * 128 : swz128(t + R2 * j2, c);
+        if (LS_IN_BOUNDS(off + sizeof(float2) <= W::stage_bytes, BS_Z_SMEM))
+          *reinterpret_cast<float2*>(sb + off) = w[j2];
+      }
     }
     fence_async_smem();
     __syncwarp();
@@ -625,6 +641,10 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
   // TMA coordinates of the item (view position iv, tile number kt of this CTA): (2 kx0 floats, ky, 0, slot)
   auto item_load = [&](int iv, int kt, int buf) {
     const int j = (int)blockIdx.x + kt * (int)gridDim.x;
+    if (!LS_IN_BOUNDS(j < ntiles && iv < nact && active_slot(s_list[iv]) < a.sel.nslots, BS_Z_TILE)) {
+      mbar_arrive(&full[buf]);   // nothing copied: the buffer's phase completes at once
+      return;
+    }
     mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
     tma_load_4d(stage + (size_t)buf * NZ * P, &a.tmap, &full[buf], 2 * (j % tiles_c) * P, j / tiles_c, 0,
                 a.slot0 + active_slot(s_list[iv]));
@@ -646,7 +666,8 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
     for (int i = tid; i < (NZ + 1) * P; i += W::NT) {
       const int kz = i / P, c2 = i % P, kx = kx0 + c2;
       const int fx = kx <= a.nx ? kx : 2 * a.nx - kx;
-      gs[kz * W::GR + c2] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+      if (LS_IN_BOUNDS(kz <= a.nz && fy >= 0 && fy <= a.ny && fx >= 0 && fx <= a.nx, BS_Z_GREEN))
+        gs[kz * W::GR + c2] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
     }
   }
   for (int i = tid; i < R1 * R2; i += W::NT) {
@@ -663,8 +684,9 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
       const int buf = i % NS;
       if (!mbar_wait_abort(&done[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZG_LIMIT)) break;
       const int j = (int)blockIdx.x + skt * (int)gridDim.x;
-      tma_store_4d(&a.tmap, stage + (size_t)buf * NZ * P, 2 * (j % tiles_c) * P, j / tiles_c, 0,
-                   a.slot0 + active_slot(s_list[sv]));
+      if (LS_IN_BOUNDS(j < ntiles && active_slot(s_list[sv]) < a.sel.nslots, BS_Z_TILE))
+        tma_store_4d(&a.tmap, stage + (size_t)buf * NZ * P, 2 * (j % tiles_c) * P, j / tiles_c, 0,
+                     a.slot0 + active_slot(s_list[sv]));
       bulk_commit();
       if (i + NS < nitems) {
         bulk_wait_read_all();   // the store has read the buffer
@@ -718,7 +740,9 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
 #pragma unroll
       for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int n1 = 0; n1 < R1 / 2; ++n1) v[n1] = *reinterpret_cast<const float2*>(sb + swz128(R2 * n1 + n2, cc));
+      for (int n1 = 0; n1 < R1 / 2; ++n1)
+        if (LS_IN_BOUNDS(swz128(R2 * n1 + n2, cc) + sizeof(float2) <= W::stage_bytes, BS_Z_SMEM))
+          v[n1] = *reinterpret_cast<const float2*>(sb + swz128(R2 * n1 + n2, cc));
       Dft<R1, -1, R1 / 2, R1>::run(v);
       const float4* tw4 = reinterpret_cast<const float4*>(twa + n2 * W::TWA);
 #pragma unroll
@@ -728,7 +752,8 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
         v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
       }
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) xc[k1 * RA + n2] = v[k1];
+      for (int k1 = 0; k1 < R1; ++k1)
+        if (LS_IN_BOUNDS(cc * W::XP + k1 * RA + n2 < P * W::XP, BS_Z_SMEM)) xc[k1 * RA + n2] = v[k1];
     }
     group_sync<W::NGRP, WG * 32>(gi);
     // forward stage 2 (thread t = k1), Green multiply, inverse stage 1 (transposed split)
@@ -779,7 +804,9 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
       }
       Dft<R1, +1, R1, R1 / 2>::run(w);
 #pragma unroll
-      for (int j2 = 0; j2 < R1 / 2; ++j2) *reinterpret_cast<float2*>(sb + swz128(j1 + R2 * j2, cc)) = w[j2];
+      for (int j2 = 0; j2 < R1 / 2; ++j2)
+        if (LS_IN_BOUNDS(swz128(j1 + R2 * j2, cc) + sizeof(float2) <= W::stage_bytes, BS_Z_SMEM))
+          *reinterpret_cast<float2*>(sb + swz128(j1 + R2 * j2, cc)) = w[j2];
     }
     fence_async_smem();
     __syncwarp();

@@ -114,3 +114,22 @@ def test_every_entry_point_rejects_bad_arguments_without_a_gpu(lib):
     assert L.ls_submit(None, None, C.byref(ticket)) == E
     assert L.ls_poll(None, 0, None) == E
     assert L.ls_last_error()   # a message for the last failure
+
+
+def test_normal_build_reports_no_index_checks_without_a_gpu(lib):
+    from paper_1910_13844_gb300 import _abi
+
+    site = ctypes.c_uint(7)
+    assert _abi.load().ls_debug_bounds(ctypes.byref(site), 1) == 0
+    assert site.value == 0
+
+
+def test_debug_build_exports_the_same_symbols(repo_root):
+    # the index-checking variant is the same library compiled with LS_DEBUG_BOUNDS (no GPU needed to build)
+    import __graft_entry__
+
+    path = __graft_entry__._build_module().build(debug=True)
+    assert path.endswith("libls_debug.so")
+    dbg = ctypes.CDLL(path)
+    missing = [n for n in _declared(repo_root) if not hasattr(dbg, n)]
+    assert not missing, missing

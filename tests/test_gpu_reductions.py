@@ -61,7 +61,7 @@ def test_norm_reduction_keeps_every_lane():
     lane = np.arange(COUNT) % 32
     pred = np.where(lane == 0, 4096.0, 1.0).astype(np.complex64)   # |d|^2 = 2^24 on lane 0, 1 elsewhere
     exact = (COUNT // 32) * (2.0 ** 24 + 31)
-    assert _float32_warp_butterfly(np.abs(pred.astype(np.float64)) ** 2) != exact
+    assert _float32_warp_butterfly(np.abs(pred).astype(np.float64) ** 2) != exact
     p = torch.from_numpy(pred).reshape(1, COUNT).cuda()
     m = torch.zeros_like(p)
     r = torch.empty_like(p)
