@@ -104,7 +104,8 @@ typedef struct {
   int z_split;                /* 1: the TMA-staged z pass with its second radix split                          */
   int strided_wide;           /* 1: the y passes with 32 pencils per CTA (else 16)                             */
   int views_per_launch;       /* BiCGStab iteration launched over chunks of this many views (0: all at once)   */
-  int z_persist;              /* 1: the TMA-staged z pass persistent (one wave of CTAs streaming their tiles)  */
+  int z_persist;              /* TMA-staged z pass persistent (one wave of CTAs): 1 tiles assigned round-robin, */
+                              /*   2 work units (a tile, a chunk of its views) taken from a counter           */
   int fx_bulk;                /* 1: the first pass with bulk-copy-staged input rows (persistent)              */
 } ls_tune;
 

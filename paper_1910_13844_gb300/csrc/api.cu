@@ -110,21 +110,42 @@ void engine_release(Engine& e) {
   e = Engine();
 }
 
-// TMA map of the engine's A2 buffers for the z pass: floats [slot][nz][2ny][4nx], box of 16 complex
-// columns x 1 row x nz planes of one slot, 128-byte swizzle.  Returns false when the driver entry
-// point is unavailable or the shape does not fit a box (the z pass then stages with cp.async).
-static bool encode_a2_map(const ls_plan* P, Engine& e) {
-  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static Encode encode = [] {
+// The driver's tensor-map encoder, looked up once through the runtime (null if unavailable).
+using TmapEncode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static TmapEncode tmap_encoder() {
+  static TmapEncode encode = [] {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess)
       fn = nullptr;
-    return reinterpret_cast<Encode>(fn);
+    return reinterpret_cast<TmapEncode>(fn);
   }();
+  return encode;
+}
+
+// TMA map of the x-unfolded Green array for the dynamically scheduled z pass: floats [nz+1][ny+1][4nx],
+// box of 16 complex columns x 1 row x (nz+1) planes, 128-byte swizzle.
+static bool encode_gxz_map(ls_plan* P) {
+  TmapEncode encode = tmap_encoder();
+  if (!encode || !P->gxz || P->nz + 1 > 256 || (2 * P->nx) % 16 != 0) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)4 * P->nx, (cuuint64_t)P->ny + 1, (cuuint64_t)P->nz + 1};
+  const cuuint64_t strides[2] = {(cuuint64_t)2 * P->nx * sizeof(float2),
+                                 (cuuint64_t)2 * P->nx * (P->ny + 1) * sizeof(float2)};
+  const cuuint32_t box[3] = {32, 1, (cuuint32_t)P->nz + 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(&P->gxz_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P->gxz, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// TMA map of the engine's A2 buffers for the z pass: floats [slot][nz][2ny][4nx], box of 16 complex
+// columns x 1 row x nz planes of one slot, 128-byte swizzle.  Returns false when the driver entry
+// point is unavailable or the shape does not fit a box (the z pass then stages with cp.async).
+static bool encode_a2_map(const ls_plan* P, Engine& e) {
+  TmapEncode encode = tmap_encoder();
   if (!encode || P->nz > 256 || (2 * P->nx) % 16 != 0) return false;
   const cuuint64_t dims[4] = {(cuuint64_t)4 * P->nx, (cuuint64_t)2 * P->ny, (cuuint64_t)P->nz, (cuuint64_t)e.cap};
   const cuuint64_t strides[3] = {(cuuint64_t)2 * P->nx * sizeof(float2),
@@ -323,7 +344,10 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   z.zwb = z.alt ? P->zwb2_z : P->zwb_z;
   z.wait_ns = (unsigned long long)P->inj_z_wait_ns;
   z.sms = P->sms;
-  z.persist = P->tune_z_persist;
+  z.persist = P->tune_z_persist >= 0 ? P->tune_z_persist : (P->gxz_ok && nslots <= kZDynMaxViews ? 2 : 0);
+  z.gmap = P->gxz_map;
+  z.gmap_ok = P->gxz_ok;
+  z.ctr = reinterpret_cast<unsigned*>(e.counts_d + 6);
   z.stall = P->inj_z_stall;
   timed(P, LS_K_Z, nslots, st, [&] { P->pz.z(z, nslots, st); });
   StridedParams iy = fy_base(P, counted(P, sel, LS_K_IY), e.a2, e.a2_stride, e.a1, e.a1_stride, P->nz);
@@ -532,8 +556,8 @@ int ensure_iter_graph(ls_plan* P, int nslots) {
   // the captured launches carry the plan's launch variants: recapture when ls_autotune changed them
   const int variant = P->tune_z_tma | P->tune_ix_prefetch << 1 | P->tune_fx_views_fastest << 2 |
                       (P->inj_z_stall || P->inj_z_wait_ns ? 1 << 3 : 0) | P->tune_z_split << 4 |
-                      P->tune_strided_wide << 5 | P->tune_z_persist << 6 | P->tune_fx_bulk << 7 |
-                      P->tune_views_per_launch << 8;
+                      P->tune_strided_wide << 5 | (P->tune_z_persist & 3) << 6 | P->tune_fx_bulk << 8 |
+                      P->tune_views_per_launch << 9;
   if (e.iter_graph && e.iter_graph_slots == nslots && e.iter_graph_variant == variant) return LS_OK;
   if (e.iter_graph) {
     cudaGraphExecDestroy(e.iter_graph);
@@ -563,6 +587,7 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   v.tune_fx_bulk = P->tune_fx_bulk;
   v.tune_views_per_launch = P->tune_views_per_launch;
   v.gocta = P->gocta; v.k2hat = P->k2hat; v.p_built = P->p_built;
+  v.gxz = P->gxz; v.gxz_map = P->gxz_map; v.gxz_ok = P->gxz_ok;
   v.device = P->device; v.sms = P->sms;
   v.tune_z_tma = P->tune_z_tma; v.tune_ix_prefetch = P->tune_ix_prefetch;
   v.tune_fx_views_fastest = P->tune_fx_views_fastest;
@@ -600,6 +625,7 @@ ls_plan* plan_clone_shared(const ls_plan* P) {
   c->tune_fx_bulk = P->tune_fx_bulk;
   c->tune_views_per_launch = P->tune_views_per_launch;
   c->gocta = P->gocta; c->k2hat = P->k2hat; c->p_built = P->p_built;
+  c->gxz = P->gxz; c->gxz_map = P->gxz_map; c->gxz_ok = P->gxz_ok;
   c->device = P->device; c->sms = P->sms;
   c->tune_z_tma = P->tune_z_tma; c->tune_ix_prefetch = P->tune_ix_prefetch;
   c->tune_fx_views_fastest = P->tune_fx_views_fastest;
@@ -917,6 +943,15 @@ int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel, c
       rc = LS_ENOMEM;
     }
   }
+  // the x-unfolded Green array of the dynamically scheduled z pass (where that pass exists); without
+  // it the z pass runs in its other forms
+  if (rc == LS_OK && P->pz.zdyn_ok && P->nz + 1 <= 256 && (2 * P->nx) % 16 == 0) {
+    if (cudaMalloc(&P->gxz, (size_t)2 * P->nx * (P->ny + 1) * (P->nz + 1) * sizeof(float2)) != cudaSuccess) {
+      cudaGetLastError();
+      P->gxz = nullptr;
+    }
+    P->gxz_ok = encode_gxz_map(P) ? 1 : 0;
+  }
   if (rc == LS_OK) rc = ls_green_spectrum(P, P->opt.oversample_p, nullptr, nullptr);
   if (rc == LS_OK) {
     double2* scratch = nullptr;
@@ -951,7 +986,7 @@ void ls_plan_destroy(ls_plan* P) {
     if (P->zwa_z != P->twa_z) { cudaFree(P->zwa_z); cudaFree(P->zwb_z); }
     cudaFree(P->zwa2_z); cudaFree(P->zwb2_z);
     cudaFree(P->twa_z); cudaFree(P->twb_z);
-    cudaFree(P->gocta); cudaFree(P->k2hat);
+    cudaFree(P->gocta); cudaFree(P->k2hat); cudaFree(P->gxz);
   }
   delete P;
 }
@@ -979,6 +1014,7 @@ int ls_green_spectrum(ls_plan* P, int p, ls_c64* out_full, void* stream) {
       return LS_ENOMEM;
     }
     cudaError_t e = build_green_octant(g, S, K, P->gocta, st);
+    if (e == cudaSuccess && P->gxz) e = unfold_octant_x(P->nx, P->ny, P->nz, P->gocta, P->gxz, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(S);
     cudaFree(K);

@@ -227,7 +227,8 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   double mv_ms = -1.0;
   if (e.a2_map_ok) mv_ms = tune_op(&cur.z_tma, 2, two);
   if (e.a2_map_ok && cur.z_tma && P->zwa2_z) mv_ms = tune_op(&cur.z_split, 2, two);
-  if (e.a2_map_ok && cur.z_tma) mv_ms = tune_op(&cur.z_persist, 2, two);
+  static const int persist3[3] = {1, 2, 0};
+  if (e.a2_map_ok && cur.z_tma) mv_ms = tune_op(&cur.z_persist, P->gxz_ok ? 3 : 2, P->gxz_ok ? persist3 : two);
   mv_ms = tune_op(&cur.strided_wide, 2, two);
   mv_ms = tune_op(&cur.ix_prefetch, 2, two);
   mv_ms = tune_op(&cur.fx_views_fastest, 2, two);

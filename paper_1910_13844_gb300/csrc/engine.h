@@ -13,6 +13,10 @@
 
 namespace lsgpu {
 
+// Untuned plans run the dynamically scheduled z pass for launches of at most this many views (it was
+// faster than one CTA per tile up to 16-30 views at 64^3-128^3, and slower at 60).
+constexpr int kZDynMaxViews = 24;
+
 enum Vec : int { V_B = 0, V_X = 1, V_R = 2, V_RH = 3, V_P = 4, V_V = 5, V_S = 6, V_T = 7, NVEC = 8 };
 
 struct Engine {
@@ -70,6 +74,9 @@ struct ls_plan {
   float2 *zwa_z = nullptr, *zwb_z = nullptr;   // z tables for the TMA-staged split (alias twa_z/twb_z if equal)
   float2 *zwa2_z = nullptr, *zwb2_z = nullptr; // z tables for its second split (null if the length has none)
   float2* gocta = nullptr;
+  float2* gxz = nullptr;        // the octant unfolded along x (dynamically scheduled z pass), if that pass exists
+  CUtensorMap gxz_map;          // TMA map of gxz (valid if gxz_ok)
+  int gxz_ok = 0;
   float2* k2hat = nullptr;
   int p_built = 0;
   bool owns_shared = true;   // false for clones that borrow another plan's spectra and twiddles
@@ -79,7 +86,9 @@ struct ls_plan {
   int tune_ix_prefetch = 1;     // IX asks L2 for its epilogue operands at kernel start
   int tune_fx_views_fastest = 0;  // FX grid with views fastest (else row blocks fastest)
   int tune_z_split = 0;           // TMA-staged z pass with its second radix split
-  int tune_z_persist = 0;         // persistent TMA-staged z pass
+  int tune_z_persist = -1;        // persistent TMA-staged z pass (0: one CTA per tile, 1: tiles round-robin,
+                                  // 2: work units from a counter; -1, untuned: 2 for launches of at most
+                                  // kZDynMaxViews views where that form exists, else 0)
   int tune_fx_bulk = 0;           // bulk-copy-staged persistent first pass
   int tune_strided_wide = 0;      // FY/IY with 32 pencils per CTA (else 16)
   int tune_views_per_launch = 0;  // BiCGStab iteration launched over chunks of this many views (0: all)

@@ -135,6 +135,19 @@ __global__ void k_expand_octant(int nx, int ny, int nz, const float2* oct, float
   }
 }
 
+// The octant unfolded along x for the dynamically scheduled z pass: gxz[kz][ky][kx] for kx in [0, 2nx)
+// (Ghat is even in kx), kz in [0, nz], ky in [0, ny]: a tile of 16 consecutive kx of one (ky) row is
+// contiguous in every kz plane, so one TMA copy fetches it.
+__global__ void k_unfold_x(int nx, int ny, int nz, const float2* oct, float2* gxz) {
+  const int Mx = 2 * nx;
+  const size_t total = (size_t)Mx * (ny + 1) * (nz + 1);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % Mx);
+    const size_t row = i / Mx;   // kz (ny + 1) + ky
+    gxz[i] = oct[row * (nx + 1) + (kx <= nx ? kx : Mx - kx)];
+  }
+}
+
 // -------------------------------------------------------------- far-field kernels
 // K2[z][dy][dx] = h^3 g(h c(dx), h c(dy), x_gamma - z_c) with g = e^{i k r}/(4 pi r)
 // (eq. def:Green, midpoint rule of eq. Gtild-1); zero at the Nyquist offsets.
@@ -313,6 +326,12 @@ cudaError_t build_green_octant(const GreenBuildParams& a, double2* S, double2* K
 cudaError_t expand_octant(int nx, int ny, int nz, const float2* oct, float2* full, cudaStream_t st) {
   const size_t total = (size_t)8 * nx * ny * nz;
   k_expand_octant<<<grid_for(total), 256, 0, st>>>(nx, ny, nz, oct, full, (float)(8.0 * nx * ny * nz));
+  return cudaGetLastError();
+}
+
+cudaError_t unfold_octant_x(int nx, int ny, int nz, const float2* oct, float2* gxz, cudaStream_t st) {
+  const size_t total = (size_t)2 * nx * (ny + 1) * (nz + 1);
+  k_unfold_x<<<grid_for(total), 256, 0, st>>>(nx, ny, nz, oct, gxz);
   return cudaGetLastError();
 }
 

@@ -58,6 +58,7 @@ struct StridedParams {
 
 struct ZParams {
   CUtensorMap tmap;            // A2 of all slots as floats [slot][nz][2ny][4nx], box {32, 1, nz, 1}, 128B swizzle
+  CUtensorMap gmap;            // x-unfolded Green array as floats [nz+1][ny+1][4nx], box {32, 1, nz+1}, 128B swizzle
   SlotSel sel;
   int nx, ny, nz;              // A2 is [nz][2ny][2nx]
   float2* a2; size_t a2_stride;
@@ -72,7 +73,9 @@ struct ZParams {
   unsigned long long wait_ns = 0;   // limit of the TMA-staged pass's per-view waits (0: one second)
   int sms = 0;                 // SMs of the device: the persistent z passes launch (resident CTAs per SM) x sms CTAs
   int alt = 0;                 // TMA-staged z pass with the second split (zwa/zwb are that split's tables)
-  int persist = 0;             // persistent TMA-staged z pass (one wave of CTAs streaming their tiles' views)
+  int persist = 0;             // persistent TMA-staged z pass: 1 tiles assigned round-robin, 2 work units from a counter
+  int gmap_ok = 0;             // gmap is valid (the dynamically scheduled form may run)
+  unsigned* ctr = nullptr;     // work-unit counter of the dynamically scheduled form (zeroed before each launch)
   int stall = 0;               // test only: the compute warps' first wait is on a barrier nothing completes
 };
 

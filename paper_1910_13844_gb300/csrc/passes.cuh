@@ -507,6 +507,7 @@ struct PassLaunch {
   int r1, r2;   // the split L = r1 * r2 of the two register stages (twiddle tables follow it)
   int zr1, zr2; // the split of the TMA-staged z pass
   int zalt_ok;  // a second split of the TMA-staged z pass exists (autotuned)
+  int zdyn_ok;  // the dynamically scheduled TMA-staged z pass exists for this length
   int zr1b, zr2b;
 };
 
@@ -563,6 +564,15 @@ struct PassImpl {
         return;
       }
     }
+    if constexpr (ZWD<L>::ok) {
+      if (a.persist == 2 && a.gmap_ok && a.ctr && a.sms > 0 && a.use_tma && (2 * a.nx) % ZWD<L>::P == 0 &&
+          a.nz <= 255) {
+        const int ntiles = (2 * a.nx / ZWD<L>::P) * (2 * a.ny);
+        cudaMemsetAsync(a.ctr, 0, sizeof(unsigned), st);
+        k_zwd<L><<<std::min(ntiles, a.sms * ZWD<L>::MINB), ZWD<L>::NT, ZWD<L>::smem, st>>>(a);
+        return;
+      }
+    }
     if constexpr (ZW<L>::ok) {
       if (a.use_tma && (2 * a.nx) % ZW<L>::P == 0 && a.nz <= 256) {
         launch_zw<false>(a, st);
@@ -587,7 +597,7 @@ struct PassImpl {
     using W = ZW<L, ALT>;
     const int ntiles = (2 * a.nx / W::P) * (2 * a.ny);
     if constexpr (W::GREG) {
-      if (a.persist && a.sms > 0) {
+      if (a.persist == 1 && a.sms > 0) {
         k_zw<L, ALT, true><<<std::min(ntiles, a.sms * W::MINB), W::NT, W::smem, st>>>(a);
         return;
       }
@@ -622,6 +632,8 @@ struct PassImpl {
         if (e == cudaSuccess) e = setup_zw<false>();
       if constexpr (ZW<L, true>::ok)
         if (e == cudaSuccess) e = setup_zw<true>();
+      if constexpr (ZWD<L>::ok)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZWD<L>::smem);
       if constexpr (ZG<L>::ok) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zg<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZG<L>::smem);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zg<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZG<L>::smem);
@@ -639,6 +651,7 @@ struct PassImpl {
     t.zr1 = ZRadix<L>::R1;
     t.zr2 = ZRadix<L>::R2;
     t.zalt_ok = ZW<L, true>::ok ? 1 : 0;
+    t.zdyn_ok = ZWD<L>::ok ? 1 : 0;
     t.zr1b = ZRadixAlt<L>::R1;
     t.zr2b = ZRadixAlt<L>::R2;
     return t;

@@ -192,6 +192,12 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, 
     }
   }
 }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_addr(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
                                             int c3) {
   asm volatile(
@@ -287,6 +293,102 @@ __device__ __forceinline__ void load_green(float2 (&g)[R2], const ZParams& a, in
     g[k2] = LS_IN_BOUNDS(kz >= 0 && kz <= a.nz && fy >= 0 && fy <= a.ny && fx >= 0 && fx <= a.nx, BS_Z_GREEN)
                 ? __ldg(col + (size_t)kz * plane)
                 : make_float2(0.f, 0.f);
+  }
+}
+
+// One view of one tile of the TMA-staged z pass, in place in its view buffer sb (TMA layout with the
+// 128-byte swizzle): forward stage 1, warp-local exchange, forward stage 2, Green multiply (conjugate
+// Green for the adjoint), inverse stage 1 (transposed split), exchange, inverse stage 2 with the crop.
+// W is the shared-memory layout; the thread owns column c as sub-transform index t (lane = t CPW +
+// column); g holds its Green values where W::GREG, else gc points at its column of the shared Green
+// tile.  adj_of() gives the view's adjoint flag; after_green() runs right after the Green multiply.
+template <class W, int L, class AdjF, class AfterF>
+__device__ __forceinline__ void zw_view(unsigned char* sb, float2* xc, const float2* twa, const float2* twb,
+                                        float2 (&g)[W::GREG ? W::R2 : 1], const float2* gc, int t, int c,
+                                        unsigned rb, bool stage2_thread, AdjF&& adj_of, AfterF&& after_green) {
+  constexpr int R1 = W::R1, R2 = W::R2, T = W::T;
+  constexpr bool GREG = W::GREG;
+  float2 u[R2];
+  if (R2 == T || t < R2) {
+    // forward stage 1: inputs z = R2 n1 + t, n1 < R1/2 (z < nz)
+    float2 v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int n1 = 0; n1 < R1 / 2; ++n1) {
+      const unsigned off = R2 % 8 == 0 ? rb + R2 * n1 * 128 : swz128(R2 * n1 + t, c);
+      if (LS_IN_BOUNDS(off + sizeof(float2) <= W::stage_bytes, BS_Z_SMEM))
+        v[n1] = *reinterpret_cast<const float2*>(sb + off);
+    }
+    Dft<R1, -1, R1 / 2, R1>::run(v);
+    const float4* tw4 = reinterpret_cast<const float4*>(twa + t * W::TWA);
+#pragma unroll
+    for (int k = 0; k < R1 / 2; ++k) {
+      const float4 w = tw4[k];
+      if (k > 0) v[2 * k] = cmul(v[2 * k], make_float2(w.x, w.y));
+      v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1)
+      if (LS_IN_BOUNDS(c * W::XP + k1 * (R2 + 2) + t < W::P * W::XP, BS_Z_SMEM)) xc[k1 * (R2 + 2) + t] = v[k1];
+  }
+  __syncwarp();
+  if (stage2_thread) {
+#pragma unroll
+    for (int q = 0; q < R2 / 2; ++q) {
+      const float4 x = *reinterpret_cast<const float4*>(xc + t * (R2 + 2) + 2 * q);
+      u[2 * q] = make_float2(x.x, x.y);
+      u[2 * q + 1] = make_float2(x.z, x.w);
+    }
+    Dft<R2, -1>::run(u);
+    // the adjoint flag is read where it is used (not held across the stages)
+    const bool adj = adj_of();
+    if constexpr (GREG) {
+      if (adj) {
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmulc(u[k2], g[k2]);
+      } else {
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmul(u[k2], g[k2]);
+      }
+      after_green();
+    } else if (adj) {
+      green_mul<true, R1, R2, L, W::GR>(u, gc, t);
+    } else {
+      green_mul<false, R1, R2, L, W::GR>(u, gc, t);
+    }
+    // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
+    Dft<R2, +1>::run(u);
+    const float4* tw4 = reinterpret_cast<const float4*>(twb + t * W::TWB);
+#pragma unroll
+    for (int k = 0; k < R2 / 2; ++k) {
+      const float4 w = tw4[k];
+      if (k > 0) u[2 * k] = cmulc(u[2 * k], make_float2(w.x, w.y));
+      u[2 * k + 1] = cmulc(u[2 * k + 1], make_float2(w.z, w.w));
+    }
+  }
+  __syncwarp();
+  if (stage2_thread) {
+#pragma unroll
+    for (int j1 = 0; j1 < R2; ++j1) xc[j1 * (R1 + 2) + t] = u[j1];
+  }
+  __syncwarp();
+  if (R2 == T || t < R2) {
+    float2 w[R1];
+#pragma unroll
+    for (int q = 0; q < R1 / 2; ++q) {
+      const float4 x = *reinterpret_cast<const float4*>(xc + t * (R1 + 2) + 2 * q);
+      w[2 * q] = make_float2(x.x, x.y);
+      w[2 * q + 1] = make_float2(x.z, x.w);
+    }
+    Dft<R1, +1, R1, R1 / 2>::run(w);
+    // outputs z = t + R2 j2 (j2 < R1/2: z < nz), in place
+#pragma unroll
+    for (int j2 = 0; j2 < R1 / 2; ++j2) {
+      const unsigned off = R2 % 8 == 0 ? rb + R2 * j2 * 128 : swz128(t + R2 * j2, c);
+      if (LS_IN_BOUNDS(off + sizeof(float2) <= W::stage_bytes, BS_Z_SMEM))
+        *reinterpret_cast<float2*>(sb + off) = w[j2];
+    }
   }
 }
 
@@ -433,99 +535,234 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
     if (!__all_sync(0xffffffffu, ok)) break;
     if (i < nact) count_run(a.sel);   // each view once per launch (by the first tile of CTA 0)
     unsigned char* sb = reinterpret_cast<unsigned char*>(stage + (size_t)buf * NZ * P);
-    float2 u[R2];
-    if (R2 == T || t < R2) {
-      // forward stage 1: inputs z = R2 n1 + t, n1 < R1/2 (z < nz)
-      float2 v[R1];
-#pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) v[n1] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int n1 = 0; n1 < R1 / 2; ++n1) {
-        const unsigned off = R2 % 8 == 0 ? rb + R2 * n1 * 128 : swz128(R2 * n1 + t, c);
-        if (LS_IN_BOUNDS(off + sizeof(float2) <= W::stage_bytes, BS_Z_SMEM))
-          v[n1] = *reinterpret_cast<const float2*>(sb + off);
-      }
-      Dft<R1, -1, R1 / 2, R1>::run(v);
-      const float4* tw4 = reinterpret_cast<const float4*>(twa + t * W::TWA);
-#pragma unroll
-      for (int k = 0; k < R1 / 2; ++k) {
-        const float4 w = tw4[k];
-        if (k > 0) v[2 * k] = cmul(v[2 * k], make_float2(w.x, w.y));
-        v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(w.z, w.w));
-      }
-#pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1)
-        if (LS_IN_BOUNDS(c * W::XP + k1 * (R2 + 2) + t < P * W::XP, BS_Z_SMEM)) xc[k1 * (R2 + 2) + t] = v[k1];
-    }
-    __syncwarp();
-    if (stage2_thread) {
-#pragma unroll
-      for (int q = 0; q < R2 / 2; ++q) {
-        const float4 x = *reinterpret_cast<const float4*>(xc + t * (R2 + 2) + 2 * q);
-        u[2 * q] = make_float2(x.x, x.y);
-        u[2 * q + 1] = make_float2(x.z, x.w);
-      }
-      Dft<R2, -1>::run(u);
-      // the adjoint flag is read from the active list where it is used (not held across the stages)
-      const bool adj = active_adj(s_list[iv]);
-      if constexpr (GREG) {
-        if (adj) {
-#pragma unroll
-          for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmulc(u[k2], g[k2]);
-        } else {
-#pragma unroll
-          for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmul(u[k2], g[k2]);
-        }
-        // last view of this tile: the next tile's Green values, in flight during the rest of this
-        // view and the forward transform of the next item
-        if (PERSIST && iv == nact - 1 && i + 1 < nitems) {
-          const int j = (int)blockIdx.x + (kt + 1) * (int)gridDim.x;
-          load_green<L, R1, R2>(g, a, j / tiles_c, (j % tiles_c) * P + c, t);
-        }
-      } else if (adj) {
-        green_mul<true, R1, R2, L, W::GR>(u, gc, t);
-      } else {
-        green_mul<false, R1, R2, L, W::GR>(u, gc, t);
-      }
-      // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
-      Dft<R2, +1>::run(u);
-      const float4* tw4 = reinterpret_cast<const float4*>(twb + t * W::TWB);
-#pragma unroll
-      for (int k = 0; k < R2 / 2; ++k) {
-        const float4 w = tw4[k];
-        if (k > 0) u[2 * k] = cmulc(u[2 * k], make_float2(w.x, w.y));
-        u[2 * k + 1] = cmulc(u[2 * k + 1], make_float2(w.z, w.w));
-      }
-    }
-    __syncwarp();
-    if (stage2_thread) {
-#pragma unroll
-      for (int j1 = 0; j1 < R2; ++j1) xc[j1 * (R1 + 2) + t] = u[j1];
-    }
-    __syncwarp();
-    if (R2 == T || t < R2) {
-      float2 w[R1];
-#pragma unroll
-      for (int q = 0; q < R1 / 2; ++q) {
-        const float4 x = *reinterpret_cast<const float4*>(xc + t * (R1 + 2) + 2 * q);
-        w[2 * q] = make_float2(x.x, x.y);
-        w[2 * q + 1] = make_float2(x.z, x.w);
-      }
-      Dft<R1, +1, R1, R1 / 2>::run(w);
-      // outputs z = t + R2 j2 (j2 < R1/2: z < nz), in place
-#pragma unroll
-      for (int j2 = 0; j2 < R1 / 2; ++j2) {
-        const unsigned off = R2 % 8 == 0 ? rb + R2 * j2 * 128 : swz128(t + R2 * j2, c);
-        if (LS_IN_BOUNDS(off + sizeof(float2) <= W::stage_bytes, BS_Z_SMEM))
-          *reinterpret_cast<float2*>(sb + off) = w[j2];
-      }
-    }
+    zw_view<W, L>(
+        sb, xc, twa, twb, g, gc, t, c, rb, stage2_thread, [&] { return active_adj(s_list[iv]); },
+        [&] {
+          // last view of this tile: the next tile's Green values, in flight during the rest of this
+          // view and the forward transform of the next item
+          if constexpr (PERSIST && W::GREG) {
+            if (iv == nact - 1 && i + 1 < nitems) {
+              const int j = (int)blockIdx.x + (kt + 1) * (int)gridDim.x;
+              load_green<L, R1, R2>(g, a, j / tiles_c, (j % tiles_c) * P + c, t);
+            }
+          }
+        });
     fence_async_smem();
     __syncwarp();
     if (lane == 0) mbar_arrive(&done[buf]);
     if (++iv == nact) { iv = 0; ++kt; }
   }
 #undef LS_ZW_LIMIT
+}
+
+// ------------------------------------------------------------------------- Z (TMA-staged, dynamic)
+// Dynamically scheduled persistent form of the TMA-staged z pass, for the splits whose Green values
+// fit in registers.  One wave of CTAs takes work units from a counter in device memory; a unit is
+// one tile with a contiguous chunk of the active views (chunks sized so that every CTA gets many
+// units: the last units finish close together).  The producer warp loads each unit's Green tile
+// with one TMA copy from the x-unfolded Green array (rows kz = 0..nz of 16 columns, 128-byte
+// swizzle) into a single shared buffer -- the compute warps copy it into registers at the unit's
+// first view, after which the next unit's tile may be loaded -- and streams the unit's views through
+// NS view buffers as k_zw does.  An item's view position and unit start are passed to the compute
+// warps in a shared ring written before the item's copy is issued; a negative entry ends the loop.
+template <int L>
+struct ZWD {
+  using B = ZW<L, false>;
+  static constexpr bool ok = B::ok && B::GREG && (L / 2) % 8 == 0 && L / 2 + 1 <= 256;
+  static constexpr int R1 = B::R1, R2 = B::R2, T = B::T, CPW = B::CPW, P = B::P, NW = B::NW, NT = B::NT;
+  static constexpr int NZ = B::NZ, MINB = B::MINB;
+  static constexpr int XP = B::XP, TWA = B::TWA, TWB = B::TWB, GR = B::GR;
+  static constexpr bool GREG = true;
+  static constexpr int NS = 3;
+  static constexpr size_t r16(size_t b) { return (b + 15) / 16 * 16; }
+  static constexpr size_t stage_bytes = B::stage_bytes;                // NZ rows of 128 bytes
+  static constexpr size_t gtile_bytes = (size_t)(NZ + 1) * 128;        // Green rows kz = 0..NZ
+  static constexpr size_t off_g = NS * stage_bytes;                    // a multiple of 1024 (NZ % 8 == 0)
+  static constexpr size_t off_x = off_g + (gtile_bytes + 1023) / 1024 * 1024;
+  static constexpr size_t x_bytes = B::x_bytes;
+  static constexpr size_t off_twa = off_x + x_bytes;
+  static constexpr size_t off_twb = off_twa + r16((size_t)R2 * TWA * sizeof(float2));
+  static constexpr size_t off_bar = off_twb + r16((size_t)R1 * TWB * sizeof(float2));
+  static constexpr int NBAR = 2 * NS + 3;                                // full[NS], done[NS], gfull, gdone, never
+  static constexpr size_t smem = off_bar + NBAR * sizeof(uint64_t) + 1024;
+};
+
+template <int L>
+__global__ void __launch_bounds__(ZWD<L>::NT, ZWD<L>::MINB) k_zwd(const __grid_constant__ ZParams a) {
+  using W = ZWD<L>;
+  constexpr int R1 = W::R1, R2 = W::R2, P = W::P, NZ = W::NZ, CPW = W::CPW, T = W::T, NW = W::NW, NS = W::NS;
+  static_assert(W::ok, "k_zwd needs a register-resident Green split");
+  extern __shared__ __align__(16) unsigned char zd_raw[];
+  const unsigned raw = smem_addr(zd_raw);
+  unsigned char* base = zd_raw + (((raw + 1023u) & ~1023u) - raw);
+  float2* stage = reinterpret_cast<float2*>(base);
+  unsigned char* gsm = base + W::off_g;
+  float2* xs = reinterpret_cast<float2*>(base + W::off_x);
+  float2* twa = reinterpret_cast<float2*>(base + W::off_twa);
+  float2* twb = reinterpret_cast<float2*>(base + W::off_twb);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + W::off_bar);   // [NS]: an item's tile has landed
+  uint64_t* done = full + NS;                                         // [NS]: the compute warps are done with it
+  uint64_t* gfull = done + NS;                                        // a unit's Green tile has landed
+  uint64_t* gdone = gfull + 1;                                        // the compute warps hold it in registers
+  uint64_t* never = gdone + 1;                                        // no thread arrives on it (stall test)
+  __shared__ int s_list[kMaxLaunchSlots];
+  __shared__ int s_ws[32];
+  __shared__ int s_abort;
+  __shared__ int s_item[NS];   // item entry: view position | unit start << 16 | tile 0 << 17; -1 ends
+  const int nact = build_active(a.sel, s_list, s_ws);
+  if (nact == 0) return;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int tiles_c = 2 * a.nx / P;
+  const int ntiles = tiles_c * 2 * a.ny;
+  // views per unit: about 16 units per CTA where the views allow, at least NS views per unit
+  int nch = (16 * (int)gridDim.x + ntiles - 1) / ntiles;
+  nch = max(1, min(nch, nact / NS));
+  const int chunk = (nact + nch - 1) / nch;
+  nch = (nact + chunk - 1) / chunk;
+  const int nunits = ntiles * nch;
+#define LS_ZD_LIMIT (a.wait_ns ? a.wait_ns : 1000000000ull)
+  if (warp == NW && lane == 0) {
+    s_abort = 0;
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&done[k], NW);
+    }
+    mbar_init(gfull, 1);
+    mbar_init(gdone, NW);
+    mbar_init(never, 1);
+    mbar_init_fence();
+  }
+  for (int i = tid; i < R1 * R2; i += W::NT) {
+    twa[(i / R1) * W::TWA + i % R1] = __ldg(a.zwa + i);
+    twb[(i / R2) * W::TWB + i % R2] = __ldg(a.zwb + i);
+  }
+  __syncthreads();
+  if (warp == NW) {
+    if (lane != 0) return;
+    // producer: units from the counter (the next id fetched one unit ahead), items in order
+    int u_next = (int)atomicAdd(a.ctr, 1u);
+    int cu = -1, cv = 0, cv_end = 0;   // unit being issued, next view position, its end
+    int ng = 0;                        // Green tiles issued
+    int st_tile[NS], st_view[NS];      // tile and view position of the item in each buffer
+    bool finished = false, failed = false;
+    // issue the next item into buffer buf; false when no work is left (the end marker is then written)
+    auto issue = [&](int buf) -> bool {
+      bool start = false;
+      if (cv >= cv_end) {
+        cu = u_next;
+        if (cu >= nunits) {
+          s_item[buf] = -1;
+          mbar_arrive(&full[buf]);   // nothing copied: the entry is visible once the phase completes
+          return false;
+        }
+        u_next = (int)atomicAdd(a.ctr, 1u);
+        const int j = cu / nch, ch = cu % nch;
+        cv = ch * chunk;
+        cv_end = min(nact, cv + chunk);
+        // the single Green buffer is free once the compute warps hold the previous tile in registers
+        if (ng > 0 && !mbar_wait_abort(gdone, (unsigned)(ng - 1) & 1u, &s_abort, LS_ZD_LIMIT)) {
+          failed = true;
+          return false;
+        }
+        const int ky = j / tiles_c;
+        const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
+        if (LS_IN_BOUNDS(j < ntiles && fy >= 0 && fy <= a.ny, BS_Z_TILE)) {
+          mbar_expect_tx(gfull, (unsigned)W::gtile_bytes);
+          tma_load_3d(gsm, &a.gmap, gfull, 2 * (j % tiles_c) * P, fy, 0);
+        } else {
+          mbar_arrive(gfull);
+        }
+        ++ng;
+        start = true;
+      }
+      const int j = cu / nch;
+      st_tile[buf] = j;
+      st_view[buf] = cv;
+      s_item[buf] = cv | (start ? 1 << 16 : 0) | (j == 0 ? 1 << 17 : 0);
+      if (LS_IN_BOUNDS(cv < nact && active_slot(s_list[cv]) < a.sel.nslots, BS_Z_TILE)) {
+        mbar_expect_tx(&full[buf], (unsigned)W::stage_bytes);
+        tma_load_4d(stage + (size_t)buf * NZ * P, &a.tmap, &full[buf], 2 * (j % tiles_c) * P, j / tiles_c, 0,
+                    a.slot0 + active_slot(s_list[cv]));
+      } else {
+        mbar_arrive(&full[buf]);
+      }
+      ++cv;
+      return true;
+    };
+    int n_issued = 0;
+    for (int k = 0; k < NS && !finished; ++k) {
+      if (issue(k)) ++n_issued;
+      else finished = true;
+    }
+    int i = 0;
+    for (; i < n_issued && !failed; ++i) {
+      const int buf = i % NS;
+      if (!mbar_wait_abort(&done[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZD_LIMIT)) {
+        failed = true;
+        break;
+      }
+      tma_store_4d(&a.tmap, stage + (size_t)buf * NZ * P, 2 * (st_tile[buf] % tiles_c) * P, st_tile[buf] / tiles_c,
+                   0, a.slot0 + active_slot(s_list[st_view[buf]]));
+      bulk_commit();
+      if (!finished) {
+        bulk_wait_read_all();   // the store has read the buffer
+        if (issue(buf)) ++n_issued;
+        else finished = true;
+      }
+    }
+    bulk_wait_read_all();
+    if (failed) {
+      // flag the launch; give the copies still in flight into this CTA's buffers (the items from i
+      // on, and the last Green tile) a bounded time to land
+      atomicExch(a.err, 1);
+      s_abort = 1;
+      for (int k = i; k < n_issued; ++k) mbar_wait(&full[k % NS], (unsigned)(k / NS) & 1u);
+      if (ng > 0) mbar_wait(gfull, (unsigned)(ng - 1) & 1u);
+    }
+    return;
+  }
+  // compute warps (as k_zw: each owns CPW whole columns, lane = t * CPW + column)
+  const int t = lane / CPW;
+  const int c = warp * CPW + lane % CPW;
+  const bool stage2_thread = R1 == T || t < R1;
+  float2* xc = xs + c * W::XP;
+  const unsigned rb = swz128(t, c);
+  float2 g[R2];
+  int ngot = 0;   // Green tiles taken
+#pragma unroll 1
+  for (int i = 0;; ++i) {
+    const int buf = i % NS;
+    const bool ok = (a.stall && i == 0) ? mbar_wait_abort(never, 0u, &s_abort, LS_ZD_LIMIT)
+                                        : mbar_wait_abort(&full[buf], (unsigned)(i / NS) & 1u, &s_abort, LS_ZD_LIMIT);
+    if (!__all_sync(0xffffffffu, ok)) break;
+    const int e = s_item[buf];
+    if (e < 0) break;
+    const int iv = e & 0xffff;
+    if (e & (1 << 16)) {
+      // first view of a unit: its Green values (kz = t + R1 k2 folded into [0, NZ]) into registers
+      const bool gok = mbar_wait_abort(gfull, (unsigned)ngot & 1u, &s_abort, LS_ZD_LIMIT);
+      if (!__all_sync(0xffffffffu, gok)) break;
+      ++ngot;
+      if (stage2_thread) {
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          const int kz = k2 < R2 / 2 ? t + R1 * k2 : L - R1 * k2 - t;
+          g[k2] = *reinterpret_cast<const float2*>(gsm + swz128(kz, c));
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(gdone);
+    }
+    count_run_if(a.sel, (e & (1 << 17)) != 0);   // each view once per launch (with tile 0)
+    unsigned char* sb = reinterpret_cast<unsigned char*>(stage + (size_t)buf * NZ * P);
+    zw_view<W, L>(sb, xc, twa, twb, g, nullptr, t, c, rb, stage2_thread, [&] { return active_adj(s_list[iv]); },
+                  [] {});
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&done[buf]);
+  }
+#undef LS_ZD_LIMIT
 }
 
 // ------------------------------------------------------------------------- Z (TMA-staged, column groups)

@@ -39,7 +39,7 @@ def test_autotune_picks_valid_variants_and_keeps_the_results(monkeypatch):
     assert t["z_tma"] in (0, 1) and t["ix_prefetch"] in (0, 1) and t["fx_views_fastest"] in (0, 1)
     assert t["check_every"] in (2, 4, 8) and t["use_graphs"] in (0, 1)
     assert t["z_split"] in (0, 1) and t["strided_wide"] in (0, 1) and t["views_per_launch"] in (0, 1, 2, 8)
-    assert t["z_persist"] in (0, 1) and t["fx_bulk"] in (0, 1)
+    assert t["z_persist"] in (0, 1, 2) and t["fx_bulk"] in (0, 1)
     assert t["matvec_us_per_view"] > 0 and t["solve_ms"] > 0
     u, far, code, stats = plan.forward(f, plan.plane_waves(k))
     torch.cuda.synchronize()
@@ -54,7 +54,8 @@ def test_autotune_picks_valid_variants_and_keeps_the_results(monkeypatch):
 # (z_tma, ix_prefetch, fx_views_fastest, check_every, use_graphs, z_split, strided_wide, views_per_launch,
 #  z_persist, fx_bulk)
 VARIANTS = [(0, 0, 0, 2, 0, 0, 0, 0, 0, 0), (1, 0, 1, 8, 1, 1, 1, 2, 0, 1), (0, 1, 0, 4, 1, 0, 1, 1, 0, 0),
-            (1, 1, 0, 2, 1, 1, 0, 0, 1, 1), (1, 1, 1, 2, 0, 0, 1, 1, 1, 0), (1, 0, 0, 4, 1, 0, 0, 2, 1, 1)]
+            (1, 1, 0, 2, 1, 1, 0, 0, 1, 1), (1, 1, 1, 2, 0, 0, 1, 1, 1, 0), (1, 0, 0, 4, 1, 0, 0, 2, 1, 1),
+            (1, 1, 0, 2, 1, 0, 0, 0, 2, 0), (1, 0, 1, 4, 0, 0, 1, 1, 2, 1)]
 NAMES = ("z_tma", "ix_prefetch", "fx_views_fastest", "check_every", "use_graphs", "z_split", "strided_wide",
          "views_per_launch", "z_persist", "fx_bulk")
 

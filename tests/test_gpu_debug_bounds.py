@@ -1,5 +1,5 @@
 """The index-checking build (libls_debug.so, compiled with LS_DEBUG_BOUNDS): on the launch variants
-of the hot path (TMA z pass in its default, second-split and persistent forms, the column-group z
+of the hot path (TMA z pass in its default, second-split, persistent and dynamically scheduled forms, the column-group z
 pass of the bead lengths, 16/32-pencil strided passes, the bulk-staged first pass, chunked
 iterations) no index check fails and the results still match the FP64 oracle; a probe that makes
 the first pass's slot check exclude one view shows that a failed check is recorded and the access
@@ -69,6 +69,9 @@ nz, ny, nx = shape
 key = torch.cuda.get_device_name().replace(" ", "_") + f":{nx}x{ny}x{nz}:4"
 open(os.environ["LS_AUTOTUNE_CACHE"], "w").write(key + " 1 1 1 2 1 1.0 1.0 1 1 2 1 1\n")
 case("variants", shape, 4, cache_line=True)
+# the dynamically scheduled z pass
+open(os.environ["LS_AUTOTUNE_CACHE"], "w").write(key + " 1 1 0 2 1 1.0 1.0 0 0 0 2 0\n")
+case("dynamic z", shape, 4, cache_line=True)
 os.environ.pop("LS_AUTOTUNE_CACHE")
 case("bead length 144", (72, 16, 16), 2)
 case("non-cubic", (24, 16, 32), 2)
@@ -108,5 +111,5 @@ def test_debug_build_checks_pass_on_every_variant_and_report_a_failed_check(tmp_
     r = subprocess.run([sys.executable, "-c", textwrap.dedent(CHILD)], env=env, capture_output=True, text=True,
                        timeout=900, cwd=ROOT)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
-    for name in ("defaults", "variants", "bead length 144", "non-cubic", "probe"):
+    for name in ("defaults", "variants", "dynamic z", "bead length 144", "non-cubic", "probe"):
         assert f"{name} ok" in r.stdout, r.stdout

@@ -135,11 +135,20 @@ def test_failed_lane_allocation_gives_enomem_and_the_server_stays_usable():
 
 
 @pytest.mark.gpu
-def test_z_pass_wait_that_runs_out_returns_ecuda_and_the_plan_stays_usable():
+@pytest.mark.parametrize("z_persist", [0, 2])
+def test_z_pass_wait_that_runs_out_returns_ecuda_and_the_plan_stays_usable(tmp_path, monkeypatch, z_persist):
     torch, ls = torch_and_lib()
     shape = (32, 32, 32)   # 64-point z transforms: the TMA-staged z pass
     f64, f, kvec = _problem(torch, shape)
     plan = ls.Plan(shape, KB, H, tol=1e-6)
+    if z_persist:
+        # the dynamically scheduled form, forced through an autotune cache entry (default variants otherwise)
+        nz, ny, nx = shape
+        key = torch.cuda.get_device_name().replace(" ", "_") + f":{nx}x{ny}x{nz}:{len(kvec)}"
+        cache = tmp_path / "tune.txt"
+        cache.write_text(key + f" 1 1 0 2 1 1.0 1.0 0 0 0 {z_persist} 0\n")
+        monkeypatch.setenv("LS_AUTOTUNE_CACHE", str(cache))
+        assert plan.autotune(len(kvec), f)["z_persist"] == z_persist
     uin = plan.plane_waves(kvec)
     ls.ls_debug_inject(plan.handle, ls.LS_INJECT_Z_STALL, 2_000_000)   # give up after 2 ms
     with pytest.raises(ls.LsError) as err:
