@@ -217,7 +217,7 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 // (both factors even, so zero padding and cropping stay whole stages).
 template <int L> struct ZRadix { static constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2; };
 template <> struct ZRadix<96>  { static constexpr int R1 = 16, R2 = 6;  };
-template <> struct ZRadix<384> { static constexpr int R1 = 12, R2 = 32; };
+template <> struct ZRadix<384> { static constexpr int R1 = 32, R2 = 12; };
 // A second split of the same length for the autotuner: the transposed one where R1 != R2, else
 // (2 R1, R2 / 2) (both factors even, thread count max(R1, R2) dividing 32 where it is usable)
 template <int L> struct ZRadixAlt {
@@ -565,15 +565,15 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
 // first view, after which the next unit's tile may be loaded -- and streams the unit's views through
 // NS view buffers as k_zw does.  An item's view position and unit start are passed to the compute
 // warps in a shared ring written before the item's copy is issued; a negative entry ends the loop.
-template <int L>
-struct ZWD {
+template <int L, int NSB>
+struct ZWDL {
   using B = ZW<L, false>;
   static constexpr bool ok = B::ok && B::GREG && (L / 2) % 8 == 0 && L / 2 + 1 <= 256;
   static constexpr int R1 = B::R1, R2 = B::R2, T = B::T, CPW = B::CPW, P = B::P, NW = B::NW, NT = B::NT;
   static constexpr int NZ = B::NZ, MINB = B::MINB;
   static constexpr int XP = B::XP, TWA = B::TWA, TWB = B::TWB, GR = B::GR;
   static constexpr bool GREG = true;
-  static constexpr int NS = 3;
+  static constexpr int NS = NSB;
   static constexpr size_t r16(size_t b) { return (b + 15) / 16 * 16; }
   static constexpr size_t stage_bytes = B::stage_bytes;                // NZ rows of 128 bytes
   static constexpr size_t gtile_bytes = (size_t)(NZ + 1) * 128;        // Green rows kz = 0..NZ
@@ -585,7 +585,13 @@ struct ZWD {
   static constexpr size_t off_bar = off_twb + r16((size_t)R1 * TWB * sizeof(float2));
   static constexpr int NBAR = 2 * NS + 3;                                // full[NS], done[NS], gfull, gdone, never
   static constexpr size_t smem = off_bar + NBAR * sizeof(uint64_t) + 1024;
+  // static shared memory of the kernel (active-view list, warp sums, flags, item ring) and the SM's share
+  static constexpr size_t static_smem = kMaxLaunchSlots * sizeof(int) + 32 * sizeof(int) + 16 + NS * sizeof(int);
+  static constexpr bool fits = (size_t)MINB * (smem + static_smem + 1024) <= 228 * 1024;
 };
+// four view buffers where the resident CTAs still fit the SM's shared memory, else three
+template <int L>
+struct ZWD : ZWDL<L, ZWDL<L, 4>::fits ? 4 : 3> {};
 
 template <int L>
 __global__ void __launch_bounds__(ZWD<L>::NT, ZWD<L>::MINB) k_zwd(const __grid_constant__ ZParams a) {

@@ -72,6 +72,28 @@ void check_groups() {
          W::smem, W::MINB);
 }
 
+// The dynamically scheduled z pass (k_zwd): view buffers, the swizzled Green tile (a TMA destination:
+// 1024-byte aligned), exchange, twiddles and barriers, for the resident CTAs its launch bounds ask for.
+template <int L>
+void check_dyn() {
+  using W = ZWD<L>;
+  if (!W::ok) return;
+  constexpr size_t static_smem = kMaxLaunchSlots * sizeof(int) + 32 * sizeof(int) + 16 + W::NS * sizeof(int);
+  static_assert(static_smem == W::static_smem, "static shared memory of k_zwd");
+  constexpr size_t sm_capacity = 228 * 1024, per_cta_max = 227 * 1024, reserved_per_cta = 1024;
+  REQUIRE(W::stage_bytes % 1024 == 0 && W::off_g % 1024 == 0, L);
+  REQUIRE(W::off_g >= (size_t)W::NS * W::stage_bytes && W::off_x >= W::off_g + W::gtile_bytes, L);
+  REQUIRE(W::off_x % 16 == 0 && W::off_twa % 16 == 0 && W::off_twb % 16 == 0 && W::off_bar % 16 == 0, L);
+  REQUIRE(W::off_twa >= W::off_x + W::x_bytes, L);
+  REQUIRE(W::off_twb >= W::off_twa + (size_t)W::R2 * W::TWA * sizeof(float2), L);
+  REQUIRE(W::off_bar >= W::off_twb + (size_t)W::R1 * W::TWB * sizeof(float2), L);
+  REQUIRE(W::NBAR == 2 * W::NS + 3 && W::smem >= W::off_bar + W::NBAR * sizeof(uint64_t) + 1023, L);
+  REQUIRE(W::NZ + 1 <= 256 && W::gtile_bytes == (size_t)(W::NZ + 1) * 128, L);   // one TMA box of Green rows
+  REQUIRE(W::smem <= per_cta_max, L);
+  REQUIRE((size_t)W::MINB * (W::smem + static_smem + reserved_per_cta) <= sm_capacity, L);
+  printf("L=%3d dynamic split %2dx%-2d NS=%d smem %6zu B x %d CTAs/SM\n", L, W::R1, W::R2, W::NS, W::smem, W::MINB);
+}
+
 int main() {
   check_groups<144>(); check_groups<288>();
   check<16>(); check<24>(); check<32>(); check<48>(); check<64>(); check<96>(); check<128>();
@@ -79,6 +101,8 @@ int main() {
   // the second splits the autotuner can choose
   check<16, true>(); check<24, true>(); check<32, true>(); check<48, true>(); check<64, true>(); check<96, true>();
   check<128, true>(); check<192, true>(); check<256, true>(); check<384, true>();
+  check_dyn<16>(); check_dyn<32>(); check_dyn<48>(); check_dyn<64>(); check_dyn<96>(); check_dyn<128>();
+  check_dyn<192>(); check_dyn<256>(); check_dyn<384>();
   printf(failures ? "FAIL\n" : "OK\n");
   return failures ? 1 : 0;
 }
