@@ -344,7 +344,8 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   z.zwb = z.alt ? P->zwb2_z : P->zwb_z;
   z.wait_ns = (unsigned long long)P->inj_z_wait_ns;
   z.sms = P->sms;
-  z.persist = P->tune_z_persist >= 0 ? P->tune_z_persist : (P->gxz_ok && nslots <= kZDynMaxViews ? 2 : 0);
+  z.persist = P->tune_z_persist >= 0 ? P->tune_z_persist
+                                     : (P->gxz_ok && (nslots <= kZDynMaxViews || P->pz.zdyn_all) ? 2 : 0);
   z.gmap = P->gxz_map;
   z.gmap_ok = P->gxz_ok;
   z.ctr = reinterpret_cast<unsigned*>(e.counts_d + 6);

@@ -227,17 +227,25 @@ template <int L> struct ZRadixAlt {
 template <int L, bool ALT> struct ZSplit { static constexpr int R1 = ZRadix<L>::R1, R2 = ZRadix<L>::R2; };
 template <int L> struct ZSplit<L, true> { static constexpr int R1 = ZRadixAlt<L>::R1, R2 = ZRadixAlt<L>::R2; };
 
+// Threads per column of the TMA-staged z pass: max(R1, R2), except at L = 384, whose 32 x 12 split
+// runs on 16 threads per column (two columns per warp, two stage-2 sub-transforms per thread) rather
+// than 32 with 20 idle lanes in the 32-point stages.
+template <int L, bool ALT> struct ZThreads { static constexpr int T = imax(ZSplit<L, ALT>::R1, ZSplit<L, ALT>::R2); };
+template <> struct ZThreads<384, false> { static constexpr int T = 16; };
+
 template <int L, bool ALT = false>
 struct ZW {
   static constexpr int R1 = ZSplit<L, ALT>::R1, R2 = ZSplit<L, ALT>::R2;
-  static constexpr int T = imax(R1, R2);
-  static constexpr bool ok = (32 % T) == 0 && R1 % 2 == 0 && R2 % 2 == 0 && R1 >= 2 && R2 >= 2;
+  static constexpr int T = ZThreads<L, ALT>::T;
+  static constexpr int S2 = (R1 + T - 1) / T;   // stage-2 sub-transforms per thread (k1 = t + T s)
+  static constexpr bool ok = (32 % T) == 0 && R1 % 2 == 0 && R2 % 2 == 0 && R1 >= 2 && R2 >= 2 && T >= R2 &&
+                             (S2 == 1 || R1 % T == 0);
   static constexpr int CPW = ok ? 32 / T : 1;   // whole columns per warp (lane = t * CPW + column)
   static constexpr int P = 16;                  // columns per CTA: one 128-byte TMA row
   static constexpr int NW = P / CPW;             // compute warps
   static constexpr int NT = 32 * NW + 32;        // + one producer warp (TMA loads and stores)
   static constexpr int NZ = L / 2;
-  static constexpr int MINB = NT >= 512 ? 1 : NT >= 256 ? 2 : 512 / NT;
+  static constexpr int MINB0 = NT >= 512 ? 1 : NT >= 256 ? 2 : 512 / NT;
   // exchange pitch per column (in float2) congruent to 16/CPW mod 16: the CPW columns of a half-warp
   // then fall on disjoint banks; the Ghat rows [kz][P + CPW] are conflict-free for the same reason
   static constexpr int pitch(int n) { return n + (((16 / CPW) - n % 16) % 16 + 16) % 16; }
@@ -246,10 +254,11 @@ struct ZW {
   static constexpr int XP = pitch(imax(R1 * (R2 + 2), R2 * (R1 + 2)));
   static constexpr int TWA = R1 + 2, TWB = R2 + 2;                            // twiddle rows (16-byte aligned)
   static constexpr int NS = 4;                                                // view buffers (TMA pipeline depth)
-  // each thread's Green values stay in registers across a tile's views where they fit (R2 <= 16); the
+  // each thread's Green values stay in registers across a tile's views where they fit (S2 R2 <= 24); the
   // Green tile is then dead once they are loaded and the exchange area reuses it, and the kernel can
   // also run persistent (Green values loaded per tile from the octant)
-  static constexpr bool GREG = R2 <= 16;
+  static constexpr bool GREG = S2 * R2 <= 24;
+  static_assert(GREG || S2 == 1, "stage-2 sub-transforms per thread need register-resident Green values");
   static constexpr size_t r16(size_t b) { return (b + 15) / 16 * 16; }       // every region 16-byte aligned
   static constexpr size_t stage_bytes = (size_t)NZ * P * sizeof(float2);
   static constexpr size_t g_bytes = r16((size_t)(NZ + 1) * GR * sizeof(float2));
@@ -261,6 +270,10 @@ struct ZW {
   static constexpr size_t off_bar = off_twb + r16((size_t)R1 * TWB * sizeof(float2));
   static constexpr int NBAR = 2 * NS + 1;                                     // full[NS], done[NS], never
   static constexpr size_t smem = off_bar + NBAR * sizeof(uint64_t) + 1024;    // + room to align the base to 1024
+  // resident CTAs asked of the launch: by threads, and no more than fit one SM's shared memory (with the
+  // kernel's static arrays and the per-CTA reserve)
+  static constexpr size_t cta_smem = smem + kMaxLaunchSlots * sizeof(int) + 32 * sizeof(int) + 16 + 1024;
+  static constexpr int MINB = MINB0 * cta_smem <= 228 * 1024 ? MINB0 : (int)(228 * 1024 / cta_smem) > 0 ? (int)(228 * 1024 / cta_smem) : 1;
 };
 
 // Byte offset of element (z, c) of a [NZ][16] complex64 tile written by TMA with the 128-byte swizzle
@@ -304,11 +317,10 @@ __device__ __forceinline__ void load_green(float2 (&g)[R2], const ZParams& a, in
 // tile.  adj_of() gives the view's adjoint flag; after_green() runs right after the Green multiply.
 template <class W, int L, class AdjF, class AfterF>
 __device__ __forceinline__ void zw_view(unsigned char* sb, float2* xc, const float2* twa, const float2* twb,
-                                        float2 (&g)[W::GREG ? W::R2 : 1], const float2* gc, int t, int c,
-                                        unsigned rb, bool stage2_thread, AdjF&& adj_of, AfterF&& after_green) {
-  constexpr int R1 = W::R1, R2 = W::R2, T = W::T;
+                                        float2 (&g)[W::S2][W::GREG ? W::R2 : 1], const float2* gc, int t, int c,
+                                        unsigned rb, AdjF&& adj_of, AfterF&& after_green) {
+  constexpr int R1 = W::R1, R2 = W::R2, T = W::T, S2 = W::S2;
   constexpr bool GREG = W::GREG;
-  float2 u[R2];
   if (R2 == T || t < R2) {
     // forward stage 1: inputs z = R2 n1 + t, n1 < R1/2 (z < nz)
     float2 v[R1];
@@ -333,44 +345,56 @@ __device__ __forceinline__ void zw_view(unsigned char* sb, float2* xc, const flo
       if (LS_IN_BOUNDS(c * W::XP + k1 * (R2 + 2) + t < W::P * W::XP, BS_Z_SMEM)) xc[k1 * (R2 + 2) + t] = v[k1];
   }
   __syncwarp();
-  if (stage2_thread) {
+  // forward stage 2, Green multiply and inverse stage 1 of sub-transforms k1 = t + T s; every row is
+  // read before any thread writes the second exchange over the first
+  float2 u[S2][R2];
 #pragma unroll
-    for (int q = 0; q < R2 / 2; ++q) {
-      const float4 x = *reinterpret_cast<const float4*>(xc + t * (R2 + 2) + 2 * q);
-      u[2 * q] = make_float2(x.x, x.y);
-      u[2 * q + 1] = make_float2(x.z, x.w);
-    }
-    Dft<R2, -1>::run(u);
-    // the adjoint flag is read where it is used (not held across the stages)
-    const bool adj = adj_of();
-    if constexpr (GREG) {
-      if (adj) {
+  for (int s2 = 0; s2 < S2; ++s2) {
+    const int k1 = t + T * s2;
+    if (R1 == T * S2 || k1 < R1) {
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmulc(u[k2], g[k2]);
-      } else {
-#pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) u[k2] = cmul(u[k2], g[k2]);
+      for (int q = 0; q < R2 / 2; ++q) {
+        const float4 x = *reinterpret_cast<const float4*>(xc + k1 * (R2 + 2) + 2 * q);
+        u[s2][2 * q] = make_float2(x.x, x.y);
+        u[s2][2 * q + 1] = make_float2(x.z, x.w);
       }
-      after_green();
-    } else if (adj) {
-      green_mul<true, R1, R2, L, W::GR>(u, gc, t);
-    } else {
-      green_mul<false, R1, R2, L, W::GR>(u, gc, t);
-    }
-    // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 t / L)
-    Dft<R2, +1>::run(u);
-    const float4* tw4 = reinterpret_cast<const float4*>(twb + t * W::TWB);
+      Dft<R2, -1>::run(u[s2]);
+      // the adjoint flag is read where it is used (not held across the stages)
+      const bool adj = adj_of();
+      if constexpr (GREG) {
+        if (adj) {
 #pragma unroll
-    for (int k = 0; k < R2 / 2; ++k) {
-      const float4 w = tw4[k];
-      if (k > 0) u[2 * k] = cmulc(u[2 * k], make_float2(w.x, w.y));
-      u[2 * k + 1] = cmulc(u[2 * k + 1], make_float2(w.z, w.w));
+          for (int k2 = 0; k2 < R2; ++k2) u[s2][k2] = cmulc(u[s2][k2], g[s2][k2]);
+        } else {
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) u[s2][k2] = cmul(u[s2][k2], g[s2][k2]);
+        }
+        if constexpr (S2 == 1) after_green();
+      } else if (adj) {
+        green_mul<true, R1, R2, L, W::GR>(u[s2], gc, k1);
+      } else {
+        green_mul<false, R1, R2, L, W::GR>(u[s2], gc, k1);
+      }
+      // inverse stage 1 (transposed split): DFT_R2 over k2, twiddle exp(+2 pi i j1 k1 / L)
+      Dft<R2, +1>::run(u[s2]);
+      const float4* tw4 = reinterpret_cast<const float4*>(twb + k1 * W::TWB);
+#pragma unroll
+      for (int k = 0; k < R2 / 2; ++k) {
+        const float4 w = tw4[k];
+        if (k > 0) u[s2][2 * k] = cmulc(u[s2][2 * k], make_float2(w.x, w.y));
+        u[s2][2 * k + 1] = cmulc(u[s2][2 * k + 1], make_float2(w.z, w.w));
+      }
     }
   }
+  if constexpr (S2 > 1) after_green();
   __syncwarp();
-  if (stage2_thread) {
 #pragma unroll
-    for (int j1 = 0; j1 < R2; ++j1) xc[j1 * (R1 + 2) + t] = u[j1];
+  for (int s2 = 0; s2 < S2; ++s2) {
+    const int k1 = t + T * s2;
+    if (R1 == T * S2 || k1 < R1) {
+#pragma unroll
+      for (int j1 = 0; j1 < R2; ++j1) xc[j1 * (R1 + 2) + k1] = u[s2][j1];
+    }
   }
   __syncwarp();
   if (R2 == T || t < R2) {
@@ -506,25 +530,31 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
   // compute warps: each owns CPW whole columns (lane = t * CPW + column)
   const int t = lane / CPW;
   const int c = warp * CPW + lane % CPW;
-  const bool stage2_thread = R1 == T || t < R1;   // threads with a stage-2 (and Green) share
+  constexpr int S2 = W::S2;
   float2* xc = xs + c * W::XP;
   const float2* gc = gs + c;
   // byte offset of (z = t + R2 j, c) in a tile: row base for j = 0, plus j R2 rows
   const unsigned rb = swz128(t, c);
-  // this thread's Green values (kz = t + R1 k2, the same for every view of a tile) in registers
-  // where they fit (R2 <= 16); longer splits read them from the shared tile for every view
-  float2 g[GREG ? R2 : 1];
+  // this thread's Green values (kz = k1 + R1 k2 for its stage-2 sub-transforms k1 = t + T s, the same
+  // for every view of a tile) in registers where they fit (S2 R2 <= 24); longer splits read them from
+  // the shared tile for every view
+  float2 g[S2][GREG ? R2 : 1];
   if constexpr (GREG) {
-    if (PERSIST && stage2_thread) {
-      load_green<L, R1, R2>(g, a, blockIdx.x / tiles_c, (blockIdx.x % tiles_c) * P + c, t);
-    } else {
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2)
-        g[k2] = stage2_thread ? (k2 < R2 / 2 ? gc[(t + R1 * k2) * W::GR] : gc[(L - R1 * k2 - t) * W::GR])
-                              : make_float2(0.f, 0.f);
-      // the exchange area overlays the Green tile: every compute warp has its values before any writes
-      if constexpr (!PERSIST) asm volatile("bar.sync 1, %0;\n" ::"r"(NW * 32) : "memory");
+    for (int s2 = 0; s2 < S2; ++s2) {
+      const int k1 = t + T * s2;
+      const bool has = R1 == T * S2 || k1 < R1;
+      if (PERSIST && has) {
+        load_green<L, R1, R2>(g[s2], a, blockIdx.x / tiles_c, (blockIdx.x % tiles_c) * P + c, k1);
+      } else if (!PERSIST) {
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2)
+          g[s2][k2] = has ? (k2 < R2 / 2 ? gc[(k1 + R1 * k2) * W::GR] : gc[(L - R1 * k2 - k1) * W::GR])
+                          : make_float2(0.f, 0.f);
+      }
     }
+    // the exchange area overlays the Green tile: every compute warp has its values before any writes
+    if constexpr (!PERSIST) asm volatile("bar.sync 1, %0;\n" ::"r"(NW * 32) : "memory");
   }
   int iv = 0, kt = 0;   // view position and tile number of item i, kept by counting
 #pragma unroll 1
@@ -536,14 +566,17 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
     if (i < nact) count_run(a.sel);   // each view once per launch (by the first tile of CTA 0)
     unsigned char* sb = reinterpret_cast<unsigned char*>(stage + (size_t)buf * NZ * P);
     zw_view<W, L>(
-        sb, xc, twa, twb, g, gc, t, c, rb, stage2_thread, [&] { return active_adj(s_list[iv]); },
+        sb, xc, twa, twb, g, gc, t, c, rb, [&] { return active_adj(s_list[iv]); },
         [&] {
           // last view of this tile: the next tile's Green values, in flight during the rest of this
           // view and the forward transform of the next item
           if constexpr (PERSIST && W::GREG) {
             if (iv == nact - 1 && i + 1 < nitems) {
               const int j = (int)blockIdx.x + (kt + 1) * (int)gridDim.x;
-              load_green<L, R1, R2>(g, a, j / tiles_c, (j % tiles_c) * P + c, t);
+#pragma unroll
+              for (int s2 = 0; s2 < S2; ++s2)
+                if (R1 == T * S2 || t + T * s2 < R1)
+                  load_green<L, R1, R2>(g[s2], a, j / tiles_c, (j % tiles_c) * P + c, t + T * s2);
             }
           }
         });
@@ -569,7 +602,7 @@ template <int L, int NSB>
 struct ZWDL {
   using B = ZW<L, false>;
   static constexpr bool ok = B::ok && B::GREG && (L / 2) % 8 == 0 && L / 2 + 1 <= 256;
-  static constexpr int R1 = B::R1, R2 = B::R2, T = B::T, CPW = B::CPW, P = B::P, NW = B::NW, NT = B::NT;
+  static constexpr int R1 = B::R1, R2 = B::R2, T = B::T, S2 = B::S2, CPW = B::CPW, P = B::P, NW = B::NW, NT = B::NT;
   static constexpr int NZ = B::NZ, MINB = B::MINB;
   static constexpr int XP = B::XP, TWA = B::TWA, TWB = B::TWB, GR = B::GR;
   static constexpr bool GREG = true;
@@ -731,10 +764,10 @@ __global__ void __launch_bounds__(ZWD<L>::NT, ZWD<L>::MINB) k_zwd(const __grid_c
   // compute warps (as k_zw: each owns CPW whole columns, lane = t * CPW + column)
   const int t = lane / CPW;
   const int c = warp * CPW + lane % CPW;
-  const bool stage2_thread = R1 == T || t < R1;
+  constexpr int S2 = W::S2;
   float2* xc = xs + c * W::XP;
   const unsigned rb = swz128(t, c);
-  float2 g[R2];
+  float2 g[S2][R2];
   int ngot = 0;   // Green tiles taken
 #pragma unroll 1
   for (int i = 0;; ++i) {
@@ -750,11 +783,15 @@ __global__ void __launch_bounds__(ZWD<L>::NT, ZWD<L>::MINB) k_zwd(const __grid_c
       const bool gok = mbar_wait_abort(gfull, (unsigned)ngot & 1u, &s_abort, LS_ZD_LIMIT);
       if (!__all_sync(0xffffffffu, gok)) break;
       ++ngot;
-      if (stage2_thread) {
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) {
-          const int kz = k2 < R2 / 2 ? t + R1 * k2 : L - R1 * k2 - t;
-          g[k2] = *reinterpret_cast<const float2*>(gsm + swz128(kz, c));
+      for (int s2 = 0; s2 < S2; ++s2) {
+        const int k1 = t + T * s2;
+        if (R1 == T * S2 || k1 < R1) {
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) {
+            const int kz = k2 < R2 / 2 ? k1 + R1 * k2 : L - R1 * k2 - k1;
+            g[s2][k2] = *reinterpret_cast<const float2*>(gsm + swz128(kz, c));
+          }
         }
       }
       __syncwarp();
@@ -762,8 +799,7 @@ __global__ void __launch_bounds__(ZWD<L>::NT, ZWD<L>::MINB) k_zwd(const __grid_c
     }
     count_run_if(a.sel, (e & (1 << 17)) != 0);   // each view once per launch (with tile 0)
     unsigned char* sb = reinterpret_cast<unsigned char*>(stage + (size_t)buf * NZ * P);
-    zw_view<W, L>(sb, xc, twa, twb, g, nullptr, t, c, rb, stage2_thread, [&] { return active_adj(s_list[iv]); },
-                  [] {});
+    zw_view<W, L>(sb, xc, twa, twb, g, nullptr, t, c, rb, [&] { return active_adj(s_list[iv]); }, [] {});
     fence_async_smem();
     __syncwarp();
     if (lane == 0) mbar_arrive(&done[buf]);

@@ -11,7 +11,7 @@ from gpu_common import H, KB, potential, rel, to_dev, torch_and_lib
 # and a config-sized non-cubic grid
 SHAPES = [(8, 8, 8), (12, 16, 24), (16, 8, 12), (32, 32, 32), (24, 48, 16), (96, 128, 128)]
 # every z transform length of the pass table: 96 and 384 run the TMA-staged z pass with their own
-# split (16 x 6, 12 x 32), 144 and 288 the cp.async-staged one
+# split (16 x 6; 32 x 12 on 16 threads per column), 144 and 288 the column-group one
 Z_LENGTHS = [(48, 24, 16), (192, 16, 16), (72, 16, 16), (144, 16, 32)]
 
 
@@ -54,6 +54,43 @@ def test_green_operator_and_matvec_match_oracle(shape, adjoint):
     f32 = fd.cpu().numpy().astype(np.float64)
     ref = x64 - kernel.apply_G_fft(Gh, f32 * x64, adjoint)
     assert rel(y.cpu().numpy(), ref) < 1e-5
+    plan.close()
+
+
+# every form of the TMA-staged z pass (split, persistence) on a batch of views, forced through an
+# autotune cache entry: 96-point (16 x 6), 384-point (32 x 12 on 16 threads per column, two stage-2
+# sub-transforms per thread) and 64-point transforms
+Z_FORMS = [(0, 0), (0, 1), (0, 2), (1, 0)]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", [(48, 24, 16), (192, 16, 16), (32, 16, 48)])
+@pytest.mark.parametrize("form", Z_FORMS)
+def test_every_z_pass_form_matches_oracle_on_a_batch(tmp_path, monkeypatch, shape, form):
+    torch, ls = torch_and_lib()
+    split, persist = form
+    nz, ny, nx = shape
+    q = 3
+    cache = tmp_path / "tune.txt"
+    key = f"{torch.cuda.get_device_name().replace(' ', '_')}:{nx}x{ny}x{nz}:{q}"
+    cache.write_text(f"{key} 1 1 0 2 1 1.0 1.0 {split} 0 0 {persist} 0\n")
+    monkeypatch.setenv("LS_AUTOTUNE_CACHE", str(cache))
+    f = potential(ph.random_ellipsoids(shape, count=4, rmin=2, rmax=max(3, min(shape) // 4)))
+    fd = to_dev(torch, f, torch.float32)
+    plan = ls.Plan(shape, KB, H)
+    t = plan.autotune(q, fd)
+    assert t["from_cache"] == 1 and t["z_persist"] == persist
+    x = torch.stack([to_dev(torch, ph.random_field(shape, 10 + i), torch.complex64) for i in range(q)])
+    Gh = kernel.green_spectrum(kernel.build_green(shape, H, KB, 4))
+    f32 = fd.cpu().numpy().astype(np.float64)
+    for adjoint in (False, True):
+        y = torch.empty_like(x)
+        ls.ls_matvec_batch(plan.handle, fd, x, y, adjoint)
+        torch.cuda.synchronize()
+        for i in range(q):
+            x64 = x[i].cpu().numpy().astype(np.complex128)
+            ref = x64 - kernel.apply_G_fft(Gh, f32 * x64, adjoint)
+            assert rel(y[i].cpu().numpy(), ref) < 1e-5, (form, adjoint, i)
     plan.close()
 
 
