@@ -344,8 +344,12 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   z.zwb = z.alt ? P->zwb2_z : P->zwb_z;
   z.wait_ns = (unsigned long long)P->inj_z_wait_ns;
   z.sms = P->sms;
-  z.persist = P->tune_z_persist >= 0 ? P->tune_z_persist
-                                     : (P->gxz_ok && (nslots <= kZDynMaxViews || P->pz.zdyn_all) ? 2 : 0);
+  if (P->tune_z_persist >= 0) {
+    z.persist = P->tune_z_persist;
+  } else {
+    const int form = nslots <= kZSmallBatch ? P->pz.zauto_small : P->pz.zauto_large;
+    z.persist = form == 2 && !P->gxz_ok ? 0 : form;
+  }
   z.gmap = P->gxz_map;
   z.gmap_ok = P->gxz_ok;
   z.ctr = reinterpret_cast<unsigned*>(e.counts_d + 6);
@@ -930,7 +934,7 @@ int ls_plan_create(const ls_grid* grid, int padding, double k_b, double voxel, c
   if (rc == LS_OK && P->pz.zalt_ok)
     rc = make_z_twiddles(L[2], P->pz.zr1b, P->pz.zr2b, &P->zwa2_z, &P->zwb2_z);
   if (rc == LS_OK) {
-    if (P->pz.zr1 == P->pz.r1) {
+    if (P->pz.zr1 == P->pz.r1 && P->pz.zr2 == P->pz.r2) {
       P->zwa_z = P->twa_z;
       P->zwb_z = P->twb_z;
     } else {

@@ -13,11 +13,6 @@
 
 namespace lsgpu {
 
-// Untuned plans run the dynamically scheduled z pass for launches of at most this many views (it was
-// faster than one CTA per tile up to 16-30 views at 64^3-128^3, and slower at 60), and at every batch
-// size for the lengths whose per-tile form fits one CTA per SM (384: faster from 1 to 60 views).
-constexpr int kZDynMaxViews = 24;
-
 enum Vec : int { V_B = 0, V_X = 1, V_R = 2, V_RH = 3, V_P = 4, V_V = 5, V_S = 6, V_T = 7, NVEC = 8 };
 
 struct Engine {
@@ -88,8 +83,7 @@ struct ls_plan {
   int tune_fx_views_fastest = 0;  // FX grid with views fastest (else row blocks fastest)
   int tune_z_split = 0;           // TMA-staged z pass with its second radix split
   int tune_z_persist = -1;        // persistent TMA-staged z pass (0: one CTA per tile, 1: tiles round-robin,
-                                  // 2: work units from a counter; -1, untuned: 2 where that form exists for
-                                  // launches of at most kZDynMaxViews views or lengths with zdyn_all, else 0)
+                                  // 2: work units from a counter; -1, untuned: the length's ZAuto form)
   int tune_fx_bulk = 0;           // bulk-copy-staged persistent first pass
   int tune_strided_wide = 0;      // FY/IY with 32 pencils per CTA (else 16)
   int tune_views_per_launch = 0;  // BiCGStab iteration launched over chunks of this many views (0: all)

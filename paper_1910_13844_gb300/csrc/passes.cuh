@@ -508,7 +508,7 @@ struct PassLaunch {
   int zr1, zr2; // the split of the TMA-staged z pass
   int zalt_ok;  // a second split of the TMA-staged z pass exists (autotuned)
   int zdyn_ok;  // the dynamically scheduled TMA-staged z pass exists for this length
-  int zdyn_all; // untuned plans run it at every batch size (its per-tile form has one CTA per SM)
+  int zauto_small, zauto_large;   // z-pass form of untuned plans up to kZSmallBatch views and above (ZAuto)
   int zr1b, zr2b;
 };
 
@@ -653,7 +653,8 @@ struct PassImpl {
     t.zr2 = ZRadix<L>::R2;
     t.zalt_ok = ZW<L, true>::ok ? 1 : 0;
     t.zdyn_ok = ZWD<L>::ok ? 1 : 0;
-    t.zdyn_all = ZWD<L>::ok && ZW<L>::MINB == 1 ? 1 : 0;
+    t.zauto_small = ZAuto<L>::small;
+    t.zauto_large = ZAuto<L>::large;
     t.zr1b = ZRadixAlt<L>::R1;
     t.zr2b = ZRadixAlt<L>::R2;
     return t;

@@ -218,6 +218,7 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 template <int L> struct ZRadix { static constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2; };
 template <> struct ZRadix<96>  { static constexpr int R1 = 16, R2 = 6;  };
 template <> struct ZRadix<384> { static constexpr int R1 = 32, R2 = 12; };
+template <> struct ZRadix<192> { static constexpr int R1 = 24, R2 = 8; };
 // A second split of the same length for the autotuner: the transposed one where R1 != R2, else
 // (2 R1, R2 / 2) (both factors even, thread count max(R1, R2) dividing 32 where it is usable)
 template <int L> struct ZRadixAlt {
@@ -232,6 +233,22 @@ template <int L> struct ZSplit<L, true> { static constexpr int R1 = ZRadixAlt<L>
 // than 32 with 20 idle lanes in the 32-point stages.
 template <int L, bool ALT> struct ZThreads { static constexpr int T = imax(ZSplit<L, ALT>::R1, ZSplit<L, ALT>::R2); };
 template <> struct ZThreads<384, false> { static constexpr int T = 16; };
+template <> struct ZThreads<128, false> { static constexpr int T = 8; };
+template <> struct ZThreads<96, false> { static constexpr int T = 8; };
+template <> struct ZThreads<192, false> { static constexpr int T = 8; };
+
+// z-pass form untuned plans run (0: one CTA per tile, 1: persistent with tiles round-robin, 2: the
+// dynamically scheduled form), for launches of at most kZSmallBatch views and above, as measured on
+// GB300 with ls_matvec_batch (z pass GB/s): 128-point (64^3 grids) the round-robin persistent form is
+// fastest from 1 to 60 views; 96-, 192- and 384-point (48^3, 96^3, 192^3) the dynamic form from 8 to 60
+// views (and within 10% of the best at one view); 256-point (128^3) the dynamic form up to about 24
+// views and one CTA per tile at 30-60.  A form a length does not have falls back to one CTA per tile.
+constexpr int kZSmallBatch = 24;
+template <int L> struct ZAuto { static constexpr int small = 2, large = 0; };
+template <> struct ZAuto<96> { static constexpr int small = 2, large = 2; };
+template <> struct ZAuto<128> { static constexpr int small = 1, large = 1; };
+template <> struct ZAuto<192> { static constexpr int small = 2, large = 2; };
+template <> struct ZAuto<384> { static constexpr int small = 2, large = 2; };
 
 template <int L, bool ALT = false>
 struct ZW {
