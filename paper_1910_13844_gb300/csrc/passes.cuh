@@ -319,8 +319,10 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 1) k_fxb(FxParams a) {
 // ------------------------------------------------------------------------- FY / IY
 // Pencils along a strided axis; tile = 16 consecutive entries of the contiguous axis.
 // P = 16 or 32 pencils per CTA (P 8-byte entries of a row: 128 or 256 contiguous bytes per load).
+// CTAs of 257-384 threads (24 threads per pencil at the 288/384-point lengths) ask for three
+// resident per SM: FY at 192^3 ran at 5.5 TB/s with two (70 registers) and 6.5 TB/s with three.
 template <int L, int DIR, int P>
-__global__ void __launch_bounds__(Geo<L>::T * P) k_strided(StridedParams a) {
+__global__ void __launch_bounds__(Geo<L>::T * P, (Geo<L>::T * P > 256 && Geo<L>::T * P <= 384) ? 3 : 1) k_strided(StridedParams a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
