@@ -42,6 +42,8 @@ WORKLOADS = {
     # the 144^3 grid of the Fig. 3 bead at lambda/16 (288-point transforms) with 16 views: the case the
     # column-group z pass is captured on
     "profile144": dict(shape=(144, 144, 144), views=16, count=20, rmin=4.0, rmax=20.0, dn_max=0.05),
+    # the 192^3 grid of the serving mix (384-point transforms) with 4 views (about 3.5 GB on the device)
+    "profile192": dict(shape=(192, 192, 192), views=4, count=20, rmin=6.0, rmax=30.0, dn_max=0.05),
 }
 TOL = 1e-6
 NA = 0.8
