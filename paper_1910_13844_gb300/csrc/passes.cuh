@@ -319,10 +319,11 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 1) k_fxb(FxParams a) {
 // ------------------------------------------------------------------------- FY / IY
 // Pencils along a strided axis; tile = 16 consecutive entries of the contiguous axis.
 // P = 16 or 32 pencils per CTA (P 8-byte entries of a row: 128 or 256 contiguous bytes per load).
-// CTAs of 257-384 threads (24 threads per pencil at the 288/384-point lengths) ask for three
-// resident per SM: FY at 192^3 ran at 5.5 TB/s with two (70 registers) and 6.5 TB/s with three.
+// CTAs of 257-384 threads (24 threads per pencil at the 288/384-point lengths) run as k_strided3, which
+// asks for three resident per SM: FY at 192^3 ran at 5.5 TB/s with two (70 registers) and 6.5 TB/s
+// with three; the other sizes keep the compiler's own register choice (k_strided).
 template <int L, int DIR, int P>
-__global__ void __launch_bounds__(Geo<L>::T * P, (Geo<L>::T * P > 256 && Geo<L>::T * P <= 384) ? 3 : 1) k_strided(StridedParams a) {
+__device__ __forceinline__ void strided_body(const StridedParams& a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
@@ -392,6 +393,12 @@ __global__ void __launch_bounds__(Geo<L>::T * P, (Geo<L>::T * P > 256 && Geo<L>:
     }
   }
 }
+
+template <int L, int DIR, int P>
+__global__ void __launch_bounds__(Geo<L>::T * P) k_strided(const StridedParams a) { strided_body<L, DIR, P>(a); }
+template <int L, int DIR, int P>
+__global__ void __launch_bounds__(Geo<L>::T * P, 3) k_strided3(const StridedParams a) { strided_body<L, DIR, P>(a); }
+template <int L, int P> struct StridedThree { static constexpr bool on = Geo<L>::T * P > 256 && Geo<L>::T * P <= 384; };
 
 // ------------------------------------------------------------------------- IX
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -550,10 +557,16 @@ struct PassImpl {
     if (a.wide && G::T * 32 <= 1024) {
       constexpr int W = G::T * 32 <= 1024 ? 32 : 16;
       dim3 blk(W, G::T), grd(((a.ncont + W - 1) / W) * a.planes, nslots);
-      k_strided<L, DIR, W><<<grd, blk, (size_t)L * W * sizeof(float2), st>>>(a);
+      if constexpr (StridedThree<L, W>::on)
+        k_strided3<L, DIR, W><<<grd, blk, (size_t)L * W * sizeof(float2), st>>>(a);
+      else
+        k_strided<L, DIR, W><<<grd, blk, (size_t)L * W * sizeof(float2), st>>>(a);
     } else {
       dim3 blk(G::PS, G::T), grd(((a.ncont + G::PS - 1) / G::PS) * a.planes, nslots);
-      k_strided<L, DIR, G::PS><<<grd, blk, G::smem_strided, st>>>(a);
+      if constexpr (StridedThree<L, G::PS>::on)
+        k_strided3<L, DIR, G::PS><<<grd, blk, G::smem_strided, st>>>(a);
+      else
+        k_strided<L, DIR, G::PS><<<grd, blk, G::smem_strided, st>>>(a);
     }
   }
   static void fy(const StridedParams& a, int nslots, cudaStream_t st) { strided<-1>(a, nslots, st); }
@@ -616,6 +629,13 @@ struct PassImpl {
         e = cudaFuncSetAttribute(k_zw<L, ALT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W::smem);
     return e;
   }
+  template <int DIR, int P>
+  static cudaError_t set_strided_smem(int bytes) {
+    if constexpr (StridedThree<L, P>::on)
+      return cudaFuncSetAttribute(k_strided3<L, DIR, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    else
+      return cudaFuncSetAttribute(k_strided<L, DIR, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  }
   static cudaError_t setup() {
     cudaError_t e = cudaSuccess;
     {
@@ -623,12 +643,12 @@ struct PassImpl {
       if constexpr (FXB<L>::ok)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fxb<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FXB<L>::smem);
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ix<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_contig);
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, -1, G::PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, +1, G::PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_strided);
+      if (e == cudaSuccess) e = set_strided_smem<-1, G::PS>((int)G::smem_strided);
+      if (e == cudaSuccess) e = set_strided_smem<+1, G::PS>((int)G::smem_strided);
       if constexpr (G::T * 32 <= 1024) {
         constexpr int sw = (int)(L * 32 * sizeof(float2));
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, -1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strided<L, +1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw);
+        if (e == cudaSuccess) e = set_strided_smem<-1, 32>(sw);
+        if (e == cudaSuccess) e = set_strided_smem<+1, 32>(sw);
       }
       if (e == cudaSuccess) e = cudaFuncSetAttribute(k_z<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_z);
       if constexpr (ZW<L>::ok)
