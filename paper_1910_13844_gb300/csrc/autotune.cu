@@ -225,10 +225,13 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   };
   static const int two[2] = {1, 0};
   double mv_ms = -1.0;
-  if (e.a2_map_ok) mv_ms = tune_op(&cur.z_tma, 2, two);
-  if (e.a2_map_ok && cur.z_tma && P->zwa2_z) mv_ms = tune_op(&cur.z_split, 2, two);
+  // the TMA-staged z pass's forms first (persistence, then the split), then TMA against the
+  // cp.async-staged pass with the best of them: at one view the per-tile TMA form and the cp.async
+  // pass are close, and only the persistent forms are fast
   static const int persist3[3] = {1, 2, 0};
-  if (e.a2_map_ok && cur.z_tma) mv_ms = tune_op(&cur.z_persist, P->gxz_ok ? 3 : 2, P->gxz_ok ? persist3 : two);
+  if (e.a2_map_ok) mv_ms = tune_op(&cur.z_persist, P->gxz_ok ? 3 : 2, P->gxz_ok ? persist3 : two);
+  if (e.a2_map_ok && P->zwa2_z) mv_ms = tune_op(&cur.z_split, 2, two);
+  if (e.a2_map_ok) mv_ms = tune_op(&cur.z_tma, 2, two);
   mv_ms = tune_op(&cur.strided_wide, 2, two);
   mv_ms = tune_op(&cur.ix_prefetch, 2, two);
   mv_ms = tune_op(&cur.fx_views_fastest, 2, two);
