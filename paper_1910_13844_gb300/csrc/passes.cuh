@@ -405,8 +405,10 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
 }
 
+// Five resident CTAs of 256 threads, six of 192 (24 or 12 threads per row): IX at 192^3 ran at 5.07
+// TB/s with five and 5.70 with six, at 144^3 4.32 and 4.89; at 128^3 six cost 15%.
 template <int L>
-__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 5) k_ix(IxParams a) {
+__global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, Geo<L>::T * Geo<L>::PC <= 192 ? 6 : 5) k_ix(IxParams a) {
   using G = Geo<L>;
   constexpr int R1 = G::R1, R2 = G::R2;
   extern __shared__ float2 sm[];
