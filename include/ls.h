@@ -239,8 +239,10 @@ int ls_prox_hs(const ls_grid* grid, const float* z, float* x, double lam, int it
  * potential f (device, N floats), one knob after the other, and keeps the fastest in the plan (the
  * plan's check_every / use_graphs options are overwritten).  If the environment variable
  * LS_AUTOTUNE_CACHE names a file, a result for the same device, grid and view count is read from it
- * instead of timing, and new results are appended to it.  Synchronous; uses the plan's workspace
- * (its contents are overwritten).  out may be NULL.  No counterpart in the paper. */
+ * instead of timing, and new results are appended to it.  The z-pass form chosen applies to launches
+ * of more than n_views / 2 views; smaller batches on the same plan keep the per-length default form
+ * (the fastest form depends on the batch size).  Synchronous; uses the plan's workspace (its
+ * contents are overwritten).  out may be NULL.  No counterpart in the paper. */
 int ls_autotune(ls_plan* plan, int n_views, const float* f, ls_tune* out, void* cuda_stream);
 
 /* Incident fields from their measurement on the detector plane (Sec. 3.4): for every plane z of

@@ -344,7 +344,7 @@ static void matvec_core(ls_plan* P, SlotSel sel, int nslots, const FxParams& fx_
   z.zwb = z.alt ? P->zwb2_z : P->zwb_z;
   z.wait_ns = (unsigned long long)P->inj_z_wait_ns;
   z.sms = P->sms;
-  if (P->tune_z_persist >= 0) {
+  if (P->tune_z_persist >= 0 && 2 * nslots > P->tune_views) {
     z.persist = P->tune_z_persist;
   } else {
     const int form = nslots <= kZSmallBatch ? P->pz.zauto_small : P->pz.zauto_large;
@@ -562,7 +562,7 @@ int ensure_iter_graph(ls_plan* P, int nslots) {
   const int variant = P->tune_z_tma | P->tune_ix_prefetch << 1 | P->tune_fx_views_fastest << 2 |
                       (P->inj_z_stall || P->inj_z_wait_ns ? 1 << 3 : 0) | P->tune_z_split << 4 |
                       P->tune_strided_wide << 5 | (P->tune_z_persist & 3) << 6 | P->tune_fx_bulk << 8 |
-                      P->tune_views_per_launch << 9;
+                      (P->tune_views_per_launch & 0x7ff) << 9 | (P->tune_views & 0x7ff) << 20;
   if (e.iter_graph && e.iter_graph_slots == nslots && e.iter_graph_variant == variant) return LS_OK;
   if (e.iter_graph) {
     cudaGraphExecDestroy(e.iter_graph);
@@ -591,6 +591,7 @@ ls_plan plan_slot_view(const ls_plan* P, int s0) {
   v.tune_z_split = P->tune_z_split; v.tune_strided_wide = P->tune_strided_wide; v.tune_z_persist = P->tune_z_persist;
   v.tune_fx_bulk = P->tune_fx_bulk;
   v.tune_views_per_launch = P->tune_views_per_launch;
+  v.tune_views = P->tune_views;
   v.gocta = P->gocta; v.k2hat = P->k2hat; v.p_built = P->p_built;
   v.gxz = P->gxz; v.gxz_map = P->gxz_map; v.gxz_ok = P->gxz_ok;
   v.device = P->device; v.sms = P->sms;
@@ -629,6 +630,7 @@ ls_plan* plan_clone_shared(const ls_plan* P) {
   c->tune_z_split = P->tune_z_split; c->tune_strided_wide = P->tune_strided_wide; c->tune_z_persist = P->tune_z_persist;
   c->tune_fx_bulk = P->tune_fx_bulk;
   c->tune_views_per_launch = P->tune_views_per_launch;
+  c->tune_views = P->tune_views;
   c->gocta = P->gocta; c->k2hat = P->k2hat; c->p_built = P->p_built;
   c->gxz = P->gxz; c->gxz_map = P->gxz_map; c->gxz_ok = P->gxz_ok;
   c->device = P->device; c->sms = P->sms;

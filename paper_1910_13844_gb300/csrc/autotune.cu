@@ -124,6 +124,9 @@ extern "C" int ls_autotune(ls_plan* P, int n_views, const float* f, ls_tune* out
   if (!P || !f || n_views < 1) { set_last_error("bad arguments"); return LS_EINVAL; }
   cudaStream_t st = (cudaStream_t)stream;
   const std::string key = tune_key(P, n_views);
+  // the z-pass form chosen here is used for launches of more than n_views / 2 views (smaller ones take
+  // the length's default form)
+  P->tune_views = n_views;
   // the workspace (and with it the z pass's TMA map) must exist before a variant is chosen
   int rc = engine_reserve(P, n_views);
   if (rc) return rc;

@@ -84,6 +84,8 @@ struct ls_plan {
   int tune_z_split = 0;           // TMA-staged z pass with its second radix split
   int tune_z_persist = -1;        // persistent TMA-staged z pass (0: one CTA per tile, 1: tiles round-robin,
                                   // 2: work units from a counter; -1, untuned: the length's ZAuto form)
+  int tune_views = 0;             // batch size ls_autotune tuned for: its z form applies to launches of
+                                  // more than tune_views / 2 views, smaller launches take the ZAuto form
   int tune_fx_bulk = 0;           // bulk-copy-staged persistent first pass
   int tune_strided_wide = 0;      // FY/IY with 32 pencils per CTA (else 16)
   int tune_views_per_launch = 0;  // BiCGStab iteration launched over chunks of this many views (0: all)
