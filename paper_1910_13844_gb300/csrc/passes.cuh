@@ -27,12 +27,14 @@
 
 namespace lsgpu {
 
-// Block reduction of NV per-thread float partial sums; thread 0 writes doubles to out[0..NV).
-// Every sum across threads is float64: the partials are gathered in shared memory, each lane of
-// the first warp adds a strided share of them in float64, and a float64 warp-shuffle tree combines
-// the 32 lanes.  Only one warp issues float64 instructions (GB300's float64 rate is low: a shuffle
-// tree in every warp cost the last FFT pass a quarter of its speed).  Blocks of at most 256
-// threads; one call per kernel (the shared array is not guarded against reuse).
+// Block reduction of NV per-thread float partial sums; out[0..NV) receives them as doubles.
+// Every sum across threads is float64: the partials are gathered in shared memory, and warp j
+// (j < NV) adds partial j of all threads, each lane a strided share in float64, combined by a
+// float64 warp-shuffle tree.  Only NV warps issue float64 instructions, one sum each, in parallel
+// (GB300's float64 rate is low: a shuffle tree of every sum in every warp cost the last FFT pass a
+// quarter of its speed, and one warp doing all NV sums lengthens the block's tail).  Blocks of at
+// least 32 NV and at most 256 threads; one call per kernel (the shared array is not guarded against
+// reuse).
 template <int NV>
 __device__ __forceinline__ void block_sum_store(const float (&acc)[NV], double* out) {
   constexpr int kMaxThreads = 256;
@@ -42,20 +44,13 @@ __device__ __forceinline__ void block_sum_store(const float (&acc)[NV], double* 
 #pragma unroll
   for (int j = 0; j < NV; ++j) part[j][tid] = acc[j];
   __syncthreads();
-  if (tid < 32) {
-    double d[NV];
+  const int j = tid >> 5, lane = tid & 31;
+  if (j < NV) {
+    double d = 0.0;
+    for (int i = lane; i < nthreads; i += 32) d += (double)part[j][i];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) d[j] = 0.0;
-    for (int i = tid; i < nthreads; i += 32)
-#pragma unroll
-      for (int j = 0; j < NV; ++j) d[j] += (double)part[j][i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int j = 0; j < NV; ++j) d[j] += __shfl_xor_sync(0xffffffffu, d[j], o);
-    if (tid == 0)
-#pragma unroll
-      for (int j = 0; j < NV; ++j) out[j] = d[j];
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0) out[j] = d;
   }
 }
 
