@@ -500,11 +500,21 @@ __global__ void __launch_bounds__(ZW<L, ALT>::NT, ZW<L, ALT>::MINB) k_zw(const _
     // one tile per CTA (the launch has one CTA per tile): its Green tile, kz folded into [0, NZ]
     const int ky = blockIdx.x / tiles_c, kx0 = (blockIdx.x % tiles_c) * P;
     const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
-    for (int i = tid; i < (NZ + 1) * P; i += W::NT) {
+    // every load of the gather is issued before any store (one L2 round trip, not one per element)
+    constexpr int GN = (NZ + 1) * P, GIT = (GN + W::NT - 1) / W::NT;
+    float2 gv[GIT];
+#pragma unroll
+    for (int r = 0; r < GIT; ++r) {
+      const int i = tid + r * W::NT;
       const int kz = i / P, cc = i % P, kx = kx0 + cc;
       const int fx = kx <= a.nx ? kx : 2 * a.nx - kx;
-      if (LS_IN_BOUNDS(kz <= a.nz && fy >= 0 && fy <= a.ny && fx >= 0 && fx <= a.nx, BS_Z_GREEN))
-        gs[kz * W::GR + cc] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+      if (i < GN && LS_IN_BOUNDS(kz <= a.nz && fy >= 0 && fy <= a.ny && fx >= 0 && fx <= a.nx, BS_Z_GREEN))
+        gv[r] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+    }
+#pragma unroll
+    for (int r = 0; r < GIT; ++r) {
+      const int i = tid + r * W::NT;
+      if (i < GN) gs[(i / P) * W::GR + i % P] = gv[r];
     }
   }
   for (int i = tid; i < R1 * R2; i += W::NT) {
@@ -959,11 +969,21 @@ __global__ void __launch_bounds__(ZG<L>::NT, ZG<L>::MINB) k_zg(const __grid_cons
     // the CTA's one tile: its Green tile, kz folded into [0, NZ]
     const int ky = blockIdx.x / tiles_c, kx0 = (blockIdx.x % tiles_c) * P;
     const int fy = ky <= a.ny ? ky : 2 * a.ny - ky;
-    for (int i = tid; i < (NZ + 1) * P; i += W::NT) {
+    // every load of the gather is issued before any store (one L2 round trip, not one per element)
+    constexpr int GN = (NZ + 1) * P, GIT = (GN + W::NT - 1) / W::NT;
+    float2 gv[GIT];
+#pragma unroll
+    for (int r = 0; r < GIT; ++r) {
+      const int i = tid + r * W::NT;
       const int kz = i / P, c2 = i % P, kx = kx0 + c2;
       const int fx = kx <= a.nx ? kx : 2 * a.nx - kx;
-      if (LS_IN_BOUNDS(kz <= a.nz && fy >= 0 && fy <= a.ny && fx >= 0 && fx <= a.nx, BS_Z_GREEN))
-        gs[kz * W::GR + c2] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+      if (i < GN && LS_IN_BOUNDS(kz <= a.nz && fy >= 0 && fy <= a.ny && fx >= 0 && fx <= a.nx, BS_Z_GREEN))
+        gv[r] = __ldg(a.gocta + ((size_t)kz * (a.ny + 1) + fy) * (a.nx + 1) + fx);
+    }
+#pragma unroll
+    for (int r = 0; r < GIT; ++r) {
+      const int i = tid + r * W::NT;
+      if (i < GN) gs[(i / P) * W::GR + i % P] = gv[r];
     }
   }
   for (int i = tid; i < R1 * R2; i += W::NT) {
