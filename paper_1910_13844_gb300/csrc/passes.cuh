@@ -217,6 +217,10 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 1) k_fxb(FxParams a) {
     for (int m = 0; m < NSTG && m < nmine; ++m) issue(m, m);
   }
   __syncthreads();
+  // this thread's stage twiddles exp(-2 pi i t k1 / L), the same for every item, in registers
+  float2 twr[R1];
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) twr[k1] = t < R2 ? __ldg(a.tw2 + k1 * R2 + t) : make_float2(0.f, 0.f);
   for (int m = 0; m < nmine; ++m) {
     const int s = m % NSTG;
     const bool ok = mbar_wait(&full[s], (unsigned)(m / NSTG) & 1u);
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(Geo<L>::T * Geo<L>::PC, 1) k_fxb(FxParams a) {
     if (t < R2) {
       Dft<R1, -1, R1 / 2, R1>::run(v);
 #pragma unroll
-      for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], __ldg(a.tw2 + k1 * R2 + t));
+      for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], twr[k1]);
 #pragma unroll
       for (int k1 = 0; k1 < R1; ++k1) S[k1 * G::SROW + t] = v[k1];
     }
