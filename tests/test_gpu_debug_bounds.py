@@ -74,6 +74,11 @@ open(os.environ["LS_AUTOTUNE_CACHE"], "w").write(key + " 1 1 0 2 1 1.0 1.0 0 0 0
 case("dynamic z", shape, 4, cache_line=True)
 os.environ.pop("LS_AUTOTUNE_CACHE")
 case("bead length 144", (72, 16, 16), 2)
+# z lengths whose threads do several stage-2 sub-transforms (128: 16 x 8 on 8 threads, 192: 24 x 8 on
+# 8, 384: 32 x 12 on 16), in the form untuned plans run for them
+case("z length 128", (64, 16, 16), 2)
+case("z length 192", (96, 16, 16), 2)
+case("z length 384", (192, 16, 16), 2)
 case("non-cubic", (24, 16, 32), 2)
 
 # a failed check: the first pass's slot check excludes the last view of the launch
@@ -111,5 +116,6 @@ def test_debug_build_checks_pass_on_every_variant_and_report_a_failed_check(tmp_
     r = subprocess.run([sys.executable, "-c", textwrap.dedent(CHILD)], env=env, capture_output=True, text=True,
                        timeout=900, cwd=ROOT)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
-    for name in ("defaults", "variants", "dynamic z", "bead length 144", "non-cubic", "probe"):
+    for name in ("defaults", "variants", "dynamic z", "bead length 144", "z length 128", "z length 192",
+                 "z length 384", "non-cubic", "probe"):
         assert f"{name} ok" in r.stdout, r.stdout
