@@ -94,6 +94,21 @@ void check_dyn() {
   printf("L=%3d dynamic split %2dx%-2d NS=%d smem %6zu B x %d CTAs/SM\n", L, W::R1, W::R2, W::NS, W::smem, W::MINB);
 }
 
+// The z-pass form untuned plans run for a length (ZAuto) exists for it: the round-robin persistent
+// form needs register-resident Green values, the dynamic form its own layout; lengths without the
+// TMA-staged pass (the bead lengths run the column-group pass) may name any form.
+template <int L>
+void check_auto() {
+  constexpr int forms[2] = {ZAuto<L>::small, ZAuto<L>::large};
+  for (int f : forms) {
+    REQUIRE(f >= 0 && f <= 2, L);
+    if (ZW<L>::ok) {
+      if (f == 1) REQUIRE(ZW<L>::GREG, L);
+      if (f == 2) REQUIRE(ZWD<L>::ok, L);
+    }
+  }
+}
+
 int main() {
   check_groups<144>(); check_groups<288>();
   check<16>(); check<24>(); check<32>(); check<48>(); check<64>(); check<96>(); check<128>();
@@ -103,6 +118,8 @@ int main() {
   check<128, true>(); check<192, true>(); check<256, true>(); check<384, true>();
   check_dyn<16>(); check_dyn<32>(); check_dyn<48>(); check_dyn<64>(); check_dyn<96>(); check_dyn<128>();
   check_dyn<192>(); check_dyn<256>(); check_dyn<384>();
+  check_auto<16>(); check_auto<24>(); check_auto<32>(); check_auto<48>(); check_auto<64>(); check_auto<96>();
+  check_auto<128>(); check_auto<144>(); check_auto<192>(); check_auto<256>(); check_auto<288>(); check_auto<384>();
   printf(failures ? "FAIL\n" : "OK\n");
   return failures ? 1 : 0;
 }
