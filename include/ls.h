@@ -56,14 +56,14 @@ enum ls_status {
   LS_ECUDA = 3,          /* a CUDA runtime call failed; see ls_last_error()               */
   LS_NOT_CONVERGED = 4,  /* max_iter reached; outputs written, stats say which view        */
   LS_BREAKDOWN = 5,      /* BiCGStab breakdown (rho or <r0,v> vanished) after all restarts */
-  LS_TIMEOUT = 6,        /* a bounded device wait expired                                  */
+  LS_TIMEOUT = 6,        /* a solve's bounded host loop ended with views still running    */
   LS_PENDING = 7,        /* ls_poll: request not finished yet                              */
   LS_EAGAIN = 8,         /* ls_submit: the request can never fit the server's HBM budget   */
   LS_ENOTFOUND = 9,      /* ls_poll: unknown or already collected ticket                   */
-  LS_EUNSUPPORTED = 10   /* grid size with no FFT length implemented (2n must be 16..384) */
+  LS_EUNSUPPORTED = 10   /* grid size with no FFT length implemented (see ls_grid)         */
 };
 
-typedef struct { int nx, ny, nz; } ls_grid;      /* voxels per axis, each in {8,12,16,24,32,48,64,96,128,192} */
+typedef struct { int nx, ny, nz; } ls_grid;      /* voxels per axis, each in {8,12,16,24,32,48,64,72,96,128,144,192} */
 typedef struct { float re, im; } ls_c64;
 
 typedef struct {
@@ -81,7 +81,7 @@ typedef struct {
 } ls_options;
 
 typedef struct {
-  int status;                 /* LS_OK, LS_NOT_CONVERGED or LS_BREAKDOWN                         */
+  int status;                 /* LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN or LS_TIMEOUT             */
   int iterations;             /* BiCGStab iterations (each has two matvecs)                      */
   int restarts;               /* restarts from the true residual                                 */
   int matvecs;                /* operator applications including residual checks                 */
@@ -104,8 +104,9 @@ typedef struct {
   int z_split;                /* 1: the TMA-staged z pass with its second radix split                          */
   int strided_wide;           /* 1: the y passes with 32 pencils per CTA (else 16)                             */
   int views_per_launch;       /* BiCGStab iteration launched over chunks of this many views (0: all at once)   */
-  int z_persist;              /* TMA-staged z pass persistent (one wave of CTAs): 1 tiles assigned round-robin, */
-                              /*   2 work units (a tile, a chunk of its views) taken from a counter           */
+  int z_persist;              /* TMA-staged z pass: 0 one CTA per tile; persistent (one wave of CTAs):         */
+                              /*   1 tiles assigned round-robin, 2 work units (a tile, a chunk of its views)   */
+                              /*   taken from a counter                                                       */
   int fx_bulk;                /* 1: the first pass with bulk-copy-staged input rows (persistent)              */
 } ls_tune;
 
@@ -184,7 +185,8 @@ int ls_matvec_noalloc(const ls_plan* plan, const float* f, const ls_c64* x, ls_c
  * solver's workspace (no caller buffer, no copies).  u_out[q] (N) and
  * far[q] (my*mx) may each be NULL (u_out == NULL: fields not returned;
  * far == NULL: far field skipped).  stats: host array of n_views or NULL.
- * Returns LS_OK, LS_NOT_CONVERGED or LS_BREAKDOWN (worst view), or an error. */
+ * Returns LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN or LS_TIMEOUT (worst view), or an error;
+ * LS_ECUDA also when a z-pass wait on its own TMA copy gave up (bounded, one second). */
 int ls_forward(ls_plan* plan, const float* f, int n_views, const ls_c64* const* u_in,
                ls_c64* const* u_out, ls_c64* const* far, ls_stats* stats, void* cuda_stream);
 

@@ -827,7 +827,7 @@ const char* ls_status_string(int status) {
     case LS_ECUDA: return "LS_ECUDA: CUDA runtime error";
     case LS_NOT_CONVERGED: return "LS_NOT_CONVERGED: max_iter reached";
     case LS_BREAKDOWN: return "LS_BREAKDOWN: BiCGStab breakdown";
-    case LS_TIMEOUT: return "LS_TIMEOUT: bounded wait expired";
+    case LS_TIMEOUT: return "LS_TIMEOUT: the solve loop ended with views still running";
     case LS_PENDING: return "LS_PENDING: request still running";
     case LS_EAGAIN: return "LS_EAGAIN: request cannot fit the memory budget";
     case LS_ENOTFOUND: return "LS_ENOTFOUND: unknown ticket";
