@@ -17,6 +17,7 @@ Reading of Alg. 1: the gradient is evaluated at the extrapolated point v^k
 """
 from __future__ import annotations
 
+import json
 import math
 import time
 from dataclasses import dataclass, field
@@ -109,17 +110,20 @@ class FistaState:
     alpha: float = 1.0
     k: int = 1
     history: list = field(default_factory=list)
+    rng: dict | None = None      # state of the generator that draws the view subsets (numpy bit generator)
 
     def save(self, path: str):
         np.savez(path, f=self.f.cpu().numpy(), f_prev=self.f_prev.cpu().numpy(), v=self.v.cpu().numpy(),
-                 alpha=self.alpha, k=self.k, history=np.array(self.history, dtype=np.float64))
+                 alpha=self.alpha, k=self.k, history=np.array(self.history, dtype=np.float64),
+                 rng=json.dumps(self.rng) if self.rng is not None else "")
 
     @staticmethod
     def load(path: str, device):
         d = np.load(path)
         t = lambda a: torch.from_numpy(a).to(device)  # noqa: E731
+        rng = str(d["rng"]) if "rng" in d.files else ""
         return FistaState(t(d["f"]), t(d["f_prev"]), t(d["v"]), float(d["alpha"]), int(d["k"]),
-                          [tuple(r) for r in d["history"]])
+                          [tuple(r) for r in d["history"]], json.loads(rng) if rng else None)
 
 
 def fista(prob: Problem, f0: torch.Tensor, iters: int, gamma0: float, tau: float, tv_iters: int = 20,
@@ -130,11 +134,14 @@ def fista(prob: Problem, f0: torch.Tensor, iters: int, gamma0: float, tau: float
 
     warm_start: start each view's forward solve from its field of the last iteration that used it.
     solver_stats: list that receives the forward solves' per-view statistics.
-    reg: "tv" (total variation) or "hs" (Hessian Schatten 1-norm), both with positivity."""
+    reg: "tv" (total variation) or "hs" (Hessian Schatten 1-norm), both with positivity.
+    A resumed run (state from a checkpoint) continues the view-subset draws where the saved run stopped."""
     prox = PROX[reg]
     rng = np.random.default_rng(seed)
     Q = prob.kvec.shape[0]
     st = state or FistaState(f0.clone(), f0.clone(), f0.clone())
+    if st.rng is not None:
+        rng.bit_generator.state = st.rng
     warm = {} if warm_start else None
     t0 = time.perf_counter()
     for _ in range(iters):
@@ -153,6 +160,7 @@ def fista(prob: Problem, f0: torch.Tensor, iters: int, gamma0: float, tau: float
             err = float((st.f - f_true).pow(2).sum() / f_true.pow(2).sum())
         st.history.append((st.k, loss, err, time.perf_counter() - t0))
         st.k += 1
+        st.rng = rng.bit_generator.state
         if checkpoint and checkpoint_every and st.k % checkpoint_every == 0:
             st.save(checkpoint)
     return st
