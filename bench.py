@@ -854,13 +854,13 @@ def run_reference(args):
            "each step: a bounded number of FP64 oracle BiCGStab iterations of one forward and one adjoint solve, "
            "scaled to 8 iterations per solve; median over steps")
     out = {
-        "metric": METRIC, "value": round(sps, 6), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": round(sps, 6), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.median([s["seconds"] for s in samples])), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": workload_name(w), "views": w["views"]},
+        "config": {"workload": workload_name(w), "views": w["views"], "oracle_processes": 1},
         "cpu_baseline": {"value": round(sps, 6), "unit": "solves/s", "cores": s0["threads"], "kind": "oracle",
-                         "sample": how},
+                         "sample": how + (f"; launched on {ws} ranks, rank 0 alone runs the oracle" if ws > 1 else "")},
         "e2e": {"value": round(sps, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
