@@ -1,6 +1,8 @@
 """Builds the in-tree CUDA library ``libls.so`` for sm_103a (no cmake, parallel nvcc)."""
 from __future__ import annotations
 
+import contextlib
+import fcntl
 import hashlib
 import os
 import subprocess
@@ -45,11 +47,29 @@ def _digest(extra=()):
     return h.hexdigest()
 
 
+@contextlib.contextmanager
+def _exclusive(path):
+    """Holds an exclusive lock on `path` (several processes of one launch may build at once: the first
+    builds, the others wait and then find the library up to date)."""
+    with open(path, "a") as fh:
+        try:
+            fcntl.flock(fh, fcntl.LOCK_EX)
+        except OSError:
+            pass   # a file system without locks: build unlocked
+        yield
+
+
 def build(verbose: bool = False, force: bool = False, debug: bool = False) -> str:
     """Compile every CUDA/C++ source of the library and link ``libls.so`` (``libls_debug.so``, the
-    index-checking variant, with debug=True); returns its path."""
-    bdir, lib, extra = (BUILD_DEBUG, LIB_DEBUG, DEBUG_FLAGS) if debug else (BUILD, LIB, [])
+    index-checking variant, with debug=True); returns its path.  Concurrent calls are serialised."""
+    bdir = BUILD_DEBUG if debug else BUILD
     os.makedirs(bdir, exist_ok=True)
+    with _exclusive(os.path.join(bdir, "lock")):
+        return _build_locked(bdir, verbose, force, debug)
+
+
+def _build_locked(bdir, verbose, force, debug):
+    lib, extra = (LIB_DEBUG, DEBUG_FLAGS) if debug else (LIB, [])
     stamp = os.path.join(bdir, "stamp")
     dig = _digest(extra)
     if not force and os.path.exists(lib) and os.path.exists(stamp) and open(stamp).read() == dig:
